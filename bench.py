@@ -1,0 +1,376 @@
+"""Benchmark: Monte Carlo Heston price + Greeks on GB300.
+
+One step = one full estimate of the multi-strike workload: 2^22 paths x 252
+steps, European + arithmetic Asian (252 equal dates) calls at K in
+{90, 100, 110} (36 estimates with standard errors), FP32 path recursion with
+FP64 sums, Philox normals, full truncation.  The step is the path kernel
+(heston_mc_launch_tiles) plus the fixed-order reduction
+(heston_mc_reduce_tiles), i.e. what heston_mc_launch enqueues.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line.  `value` is path-steps/s over all ranks with inputs
+resident on the device; `e2e` is the same metric through the synchronous
+host API (heston_mc_price_greeks_ex: host structs in, results copied back).
+`--impl reference` times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "path-steps/s at fixed std error (Greek-sets/s alongside)"
+UNIT = "path-steps/s"
+
+# Algorithmic thread-instructions per path-step for this workload (FP32 path,
+# full truncation, European + Asian with a date every step, Vega/Theta
+# tangents, Gamma weights): Philox4x32-10 half call 30, uniforms 6,
+# Box-Muller 9 (4 MUFU), correlation 4, truncation + sqrt 8, tangent du 5,
+# Gamma weights 2, ln S step 3, ln S tangents 5, V step 8, V tangents 10,
+# Asian date 7 (1 MUFU), loop 1.  Total 98, of which 6 on the MUFU pipe.
+ALGO_INSTR_PER_PATH_STEP = 98
+ISSUE_LANES_PER_SM_CLK = 128          # 4 SM sub-partitions x 1 warp-instruction x 32 lanes
+FLUSH_BYTES = 256 << 20               # > 129 MB L2
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "heston_paths_kernel_multi_strike_2p22.md")
+KERNEL_SOURCE = os.path.join(ROOT, "paper_2309_10477_gb300", "csrc", "heston_mc.cu")
+
+
+def _dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def _measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.rows = []
+        self.marks = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append((time.time(), [x.strip() for x in line.split(",")]))
+
+    def mark(self, on: bool):
+        self.marks.append((time.time(), on))
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        windows = []
+        for (t0, a), (t1, b) in zip(self.marks[::2], self.marks[1::2]):
+            windows.append((t0, t1))
+        inside = [r for t, r in self.rows if any(a <= t <= b for a, b in windows)]
+        rows = inside or [r for _, r in self.rows]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"],
+                    "samples": 0}
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4)
+                          if len(r) > 5 + i and r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max((num(r[3]) or 0.0) for r in rows)}
+
+
+def _source_hash():
+    return hashlib.sha256(open(KERNEL_SOURCE, "rb").read()).hexdigest()[:16]
+
+
+def _profiled_traffic():
+    """DRAM bytes per launch of the path kernel from the committed ncu summary,
+    or None if the kernel source changed since it was captured."""
+    try:
+        text = open(PROFILE_SUMMARY).read()
+    except OSError:
+        return None
+    m = re.search(r"source sha256\[:16\]:\s*([0-9a-f]{16})", text)
+    t = re.search(r"dram bytes per full launch:\s*([0-9.eE+]+)", text)
+    if not m or not t or m.group(1) != _source_hash():
+        return None
+    return float(t.group(1))
+
+
+# ---------------------------------------------------------------------------
+# Oracle (CPU) timing -- the reported baseline and the reference arm
+# ---------------------------------------------------------------------------
+
+def _oracle_sample(target_s: float):
+    import oracle
+    from paper_2309_10477_gb300 import workloads as wl
+    w = wl.multi_strike_fp32()
+    P = oracle.Params(**w.params)
+    cs = [oracle.Contract(c[0], c[1], c[2], c[3], c[4]) for c in w.contracts]
+    threads = oracle.max_threads()
+    n = 4096 * threads
+    oracle.mc_sums(P, cs, n, w.n_steps, w.seed)          # warm the threads
+    t0 = time.perf_counter()
+    oracle.mc_sums(P, cs, n, w.n_steps, w.seed)
+    dt = time.perf_counter() - t0
+    n_sample = int(min(n * target_s / max(dt, 1e-6), w.n_paths))
+    n_sample = max(4096, (n_sample // 4096) * 4096)
+    return w, P, cs, threads, n_sample
+
+
+def _time_oracle(w, P, cs, n_sample, reps=1):
+    import oracle
+    best = None
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        oracle.mc_sums(P, cs, n_sample, w.n_steps, w.seed)
+        dt = time.perf_counter() - t0
+        best = dt if best is None else min(best, dt)
+    return n_sample * w.n_steps / best, best
+
+
+def cpu_baseline(target_s: float = 10.0):
+    w, P, cs, threads, n = _oracle_sample(target_s)
+    rate, dt = _time_oracle(w, P, cs, n)
+    return {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{n} of the {w.n_paths} paths x {w.n_steps} steps, 6 contracts, FP64 "
+                      f"oracle on {threads} host threads ({dt:.1f} s)"}
+
+
+def run_reference(args):
+    rank, world, _ = _dist_env()
+    if rank != 0:
+        return 0
+    per_step_s = max(1.0, 120.0 / max(1, args.steps + args.warmup))
+    w, P, cs, threads, n = _oracle_sample(per_step_s)
+    for _ in range(args.warmup):
+        _time_oracle(w, P, cs, n)
+    times = []
+    for _ in range(args.steps):
+        _, dt = _time_oracle(w, P, cs, n)
+        times.append(dt)
+    step_s = statistics.mean(times)
+    value = n * w.n_steps / step_s
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": w.name, "n_paths_per_step": n, "n_steps": w.n_steps,
+                   "contracts": 6, "sample": f"{n} of {w.n_paths} paths per step"},
+        "greek_sets_per_s": 6.0 / step_s,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{n} paths x {w.n_steps} steps per step, FP64 oracle"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_gpu(args):
+    import ctypes
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2309_10477_gb300 import native as nv
+    from paper_2309_10477_gb300 import workloads as wl
+
+    rank, world, local = _dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    lib = nv.load()
+    stream = torch.cuda.current_stream()
+
+    w = wl.multi_strike_fp32()
+    nc = len(w.contracts)
+    params = nv.make_params(**w.params)
+    contracts = [nv.make_contract(*c) for c in w.contracts]
+    opts = nv.make_options(prec=nv.HESTON_FP32, stream=stream, device=local)
+    n = args.n_paths or w.n_paths
+    path_begin = rank * n                       # weak scaling: one path range per rank
+    n_tiles = -(-n // nv.HESTON_TILE_PATHS)
+    rows = torch.empty(n_tiles * 12 * nc, dtype=torch.float64, device=dev)
+    ws_bytes = nv.heston_mc_workspace_bytes(nc, n)
+    ws = torch.empty(ws_bytes // 8, dtype=torch.float64, device=dev)
+    out = torch.empty(nc * 12, dtype=torch.float64, device=dev)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        nv.heston_mc_launch_tiles(params, contracts, path_begin, n, w.n_steps, w.seed, opts, rows)
+        if ev is not None:
+            ev[1].record(stream)
+        nv.heston_mc_reduce_tiles(rows, n_tiles, nc, n, ws, ws_bytes, out, stream)
+        if ev is not None:
+            ev[2].record(stream)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    barrier()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    events = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    barrier()
+    clocks.mark(True)
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)                    # evict L2 between timed steps (outside events)
+        step(events[i])
+    barrier()
+    clocks.mark(False)
+    step_ms = [e[0].elapsed_time(e[2]) for e in events]
+    k1_ms = [e[0].elapsed_time(e[1]) for e in events]
+    local_ms = statistics.mean(step_ms)
+    local_k1 = statistics.mean(k1_ms)
+    t = torch.tensor([local_ms, local_k1], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms, k1 = float(t[0]), float(t[1])
+    estimates = out.view(nc, 12).cpu().numpy()
+
+    # end to end through the synchronous host API (host structs in, results out)
+    res_arr = (nv.heston_result * nc)()
+    carr = (nv.heston_contract * nc)(*contracts)
+    e2e_opts = nv.make_options(prec=nv.HESTON_FP32, stream=stream, device=local)
+    for _ in range(2):
+        lib.heston_mc_price_greeks_ex(ctypes.byref(params), carr, nc, n, w.n_steps, w.seed,
+                                      ctypes.byref(e2e_opts), res_arr)
+    barrier()
+    clocks.mark(True)
+    e2e_steps = max(3, min(args.steps, 20))
+    e2e_times = []
+    for _ in range(e2e_steps):
+        t0 = time.perf_counter()
+        rc = lib.heston_mc_price_greeks_ex(ctypes.byref(params), carr, nc, n, w.n_steps, w.seed,
+                                           ctypes.byref(e2e_opts), res_arr)
+        e2e_times.append(time.perf_counter() - t0)
+        assert rc >= 0, nv.heston_status_string(rc)
+    clocks.mark(False)
+    clocks.stop()
+    e2e_s = torch.tensor([statistics.mean(e2e_times)], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(e2e_s, op=dist.ReduceOp.MAX)
+
+    path_steps = n * w.n_steps
+    value = world * path_steps / (ms * 1e-3)
+    if rank == 0:
+        peaks = _measured_peaks()
+        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        clk = clocks.summary()
+        max_mhz = float(peaks.get("sm_max_mhz") or clk.get("sm_max_mhz") or 2070.0)
+        peak_tinst = n_sm * ISSUE_LANES_PER_SM_CLK * max_mhz * 1e6 / 1e12
+        achieved_tinst = path_steps * ALGO_INSTR_PER_PATH_STEP / (k1 * 1e-3) / 1e12
+        traffic = _profiled_traffic()
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": w.name if n == w.n_paths else f"{w.name} (n_paths={n})",
+                       "n_paths": n, "n_steps": w.n_steps,
+                       "contracts": "European + Asian(M=252) calls, K in {90,100,110}",
+                       "estimates": 6 * nc, "truncation": "full", "rng": "philox4x32-10",
+                       "precision": "fp32 path, fp64 sums", "parallelism": f"dp{world} (path ranges)",
+                       "l2": "flushed between timed steps (256 MiB write outside the events)"},
+            "greek_sets_per_s": world * nc / (ms * 1e-3),
+            "price_se_k100_euro": float(estimates[1, 6]),
+            "fixed_se_note": "SE target = the FP64 oracle's SE on the same normals; the GPU SE "
+                             "matches it to 1e-3 (tested), so time-to-target = time per step",
+            "e2e": {"value": world * path_steps / float(e2e_s[0]), "unit": UNIT,
+                    "h2d_bytes_per_step": ctypes.sizeof(nv.heston_params)
+                    + nc * ctypes.sizeof(nv.heston_contract),
+                    "d2h_bytes_per_step": nc * 12 * 8},
+            "gpu_launches": 3 * args.steps,
+            "roofline": {"bound": "alu", "kernel": "heston_paths_kernel<float,FULL,ASIAN>",
+                         "achieved": achieved_tinst, "peak": peak_tinst,
+                         "unit": f"T thread-instr/s ({ALGO_INSTR_PER_PATH_STEP} algorithmic per "
+                                 f"path-step; peak = {n_sm} SMs x 128 lanes x {max_mhz:.0f} MHz)",
+                         "frac": achieved_tinst / peak_tinst, "traffic": traffic,
+                         "kernel_ms": k1,
+                         "path_steps_per_s_kernel": path_steps / (k1 * 1e-3)},
+            "clocks": clk,
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--n-paths", type=int, default=0,
+                    help="paths per rank (default: the workload's 2^22); small cases for ncu")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,210 @@
+/*
+ * heston_mc.h -- C ABI of the GB300 Monte Carlo Heston pricer (arXiv 2309.10477).
+ *
+ * The library simulates Heston paths (Eq. heston_eq, Sec. 2.3) with the
+ * Milstein scheme for ln S and V (Sec. 2.4.2, Algorithm "Milstein
+ * approximation under Heston model"), driven by correlated normals
+ * (Algorithm "Generation of two correlated Normal random variables"), and
+ * returns Monte Carlo estimates (Algorithm "Monte Carlo option pricing
+ * estimation", Sec. 2.5) of the discounted price and the Greeks Delta,
+ * Gamma, Vega, Rho and Theta (named in Sec. 2.2; pathwise Delta and Rho of
+ * Eq. euro_pw and Eq. asian_pw) with their standard errors, all from the
+ * same paths.  Every path lives in registers on the GPU; nothing per path
+ * is written to memory.
+ *
+ * Conventions for every entry point:
+ *   - Pointers documented "host" point to caller-owned host memory; pointers
+ *     documented "device" point to caller-owned memory on the selected CUDA
+ *     device.  The library never retains a pointer after a call returns.
+ *   - Return value: HESTON_OK (0) on success, a positive HESTON_WARN_* code
+ *     when results are produced but some are undefined (set to NaN), or a
+ *     negative HESTON_ERR_* code; on error nothing is launched and no output
+ *     is written unless stated.  No C++ exception crosses this interface.
+ *   - Calls on different streams may run concurrently from different host
+ *     threads; the library holds no global mutable state.
+ *
+ * Random numbers (the contract both the GPU path and the test oracle
+ * implement): Philox4x32-10 (Salmon et al., SC'11) with key = rng_seed
+ * (low word first) and counter = (step / 2, path_lo, path_hi, 0) for path
+ * index `path` and time step `step`; words 0-1 feed even steps and words
+ * 2-3 odd steps as (u1, u2) with u1 = ((w >> 8) + 1) * 2^-24 and
+ * u2 = (w >> 8) * 2^-24; Box-Muller Za = sqrt(-2 ln u1) cos(2 pi u2),
+ * Zb = sqrt(-2 ln u1) sin(2 pi u2).  Results are therefore a function of
+ * (inputs, seed) only, independent of launch shape, device and sharding.
+ */
+#ifndef HESTON_MC_H
+#define HESTON_MC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ----------------------------------------------------- */
+#define HESTON_OK                    0
+#define HESTON_WARN_GAMMA_UNDEFINED  1  /* |rho| == 1 or v0 == 0: Gamma (and its SE) set to NaN */
+#define HESTON_ERR_INVALID_ARG      -1  /* a parameter is out of its domain (see heston_mc_price_greeks_ex) */
+#define HESTON_ERR_CUDA             -2  /* a CUDA runtime call failed */
+#define HESTON_ERR_NOMEM            -3  /* device allocation failed */
+#define HESTON_ERR_TIMEOUT          -4  /* reserved: a bounded device wait expired */
+#define HESTON_ERR_CANCELLED        -5  /* reserved: a cancel flag was raised */
+#define HESTON_ERR_UNSUPPORTED      -6  /* option combination not built */
+#define HESTON_ERR_WORKSPACE        -7  /* caller workspace missing, misaligned or too small */
+
+#define HESTON_MAX_CONTRACTS 8          /* contracts priced on one set of paths */
+#define HESTON_TILE_PATHS   64          /* paths per deterministic partial sum */
+
+/* ---- inputs ------------------------------------------------------------ */
+
+/* Heston parameters (Eq. heston_eq and Table "Heston model parameters"):
+ * dS = r S dt + sqrt(V) S dW1, dV = kappa (theta - V) dt + xi sqrt(V) dW2,
+ * corr(dW1, dW2) = rho.  The paper writes sigma for xi. */
+typedef struct {
+    double S0, v0, kappa, theta, xi, rho, r;
+} heston_params;
+
+typedef enum { HESTON_EUROPEAN = 0, HESTON_ASIAN_ARITH = 1 } heston_payoff;
+
+/* One option.  European payoff max(S_T - K, 0) (put: max(K - S_T, 0));
+ * arithmetic Asian payoff on Sbar = (1/M) sum_{i=1..M} S_{t_i} with equal
+ * dates t_i = i T / M (Sec. 2.1).  n_monitor = M; 0 means M = n_steps;
+ * n_steps must be a multiple of M. */
+typedef struct {
+    int32_t payoff;      /* heston_payoff */
+    int32_t is_put;      /* 0 = call, 1 = put */
+    double K;            /* strike, >= 0 */
+    double T;            /* maturity in years, > 0 */
+    uint32_t n_monitor;  /* Asian dates M (0 = every step) */
+    uint32_t reserved;   /* must be 0 */
+} heston_contract;
+
+typedef enum { HESTON_TRUNC_FULL = 0, HESTON_TRUNC_PAPER_FLOOR = 1 } heston_trunc;
+typedef enum { HESTON_RNG_PHILOX = 0, HESTON_RNG_SOBOL_BB = 1 } heston_rng;
+typedef enum { HESTON_FP32 = 0, HESTON_FP64 = 1 } heston_prec;
+
+/* Options.  trunc: full truncation (the state keeps its sign; drift,
+ * diffusion and the Milstein term see max(V, 0)) or the paper's floor
+ * V = max(V, 0) after each update (Sec. 2.4.2).  prec: arithmetic of the
+ * path recursion; sums are always FP64 above the 64-path tile.
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream).  device:
+ * CUDA ordinal, or -1 for the calling thread's current device.
+ * grid_ctas / block_threads: launch shape of the path kernel (0 = choose);
+ * results do not depend on them.  n_shifts: reserved for the QMC variant. */
+typedef struct {
+    int32_t trunc;
+    int32_t rng;
+    int32_t prec;
+    uint32_t n_shifts;
+    void *cuda_stream;
+    int32_t device;
+    uint32_t grid_ctas;
+    uint32_t block_threads;
+    uint32_t reserved;
+} heston_options;
+
+/* Result for one contract: discounted price, Delta = dV/dS0,
+ * Gamma = d2V/dS0^2, Vega = dV/dv0, Rho = dV/dr, Theta = -dV/dT, and the
+ * standard error of each mean (sample stdev / sqrt(n)), se[] in the same
+ * order.  The first 12 doubles match the device output layout below. */
+typedef struct {
+    double price, delta, gamma, vega, rho, theta;
+    double se[6];
+    uint64_t n_paths;
+    int32_t status;
+    int32_t reserved;
+} heston_result;
+
+/* ---- synchronous host API ------------------------------------------------ */
+
+/* Price one contract with the defaults (full truncation, Philox, FP64 path,
+ * legacy default stream, current device).  params, contract, out: host.
+ * Blocks until the result is in *out.  out->status mirrors the return. */
+int heston_mc_price_greeks(const heston_params *params, const heston_contract *contract,
+                           uint64_t n_paths, uint32_t n_steps, uint64_t rng_seed,
+                           heston_result *out);
+
+/* Price n_contracts (1..HESTON_MAX_CONTRACTS) options on the same n_paths
+ * paths of n_steps steps.  All contracts must share T; Asian contracts must
+ * share M.  opts may be NULL (defaults).  out: host array of n_contracts.
+ * Allocates its device workspace stream-ordered on opts->cuda_stream, and
+ * returns after that stream has produced the results.
+ * HESTON_ERR_INVALID_ARG when: a pointer is NULL; S0 <= 0; K < 0; T <= 0;
+ * v0, theta, kappa or xi < 0; |rho| > 1; any value not finite; n_steps == 0;
+ * n_paths < 2 or > 2^40; N % M != 0; contracts disagree on T or on M;
+ * payoff or is_put out of range; an enum or reserved field out of range. */
+int heston_mc_price_greeks_ex(const heston_params *params, const heston_contract *contracts,
+                              uint32_t n_contracts, uint64_t n_paths, uint32_t n_steps,
+                              uint64_t rng_seed, const heston_options *opts,
+                              heston_result *out);
+
+/* ---- asynchronous device API (no allocation, no synchronisation) -------- */
+
+/* Bytes of device workspace heston_mc_launch needs for these sizes. */
+int heston_mc_workspace_bytes(uint32_t n_contracts, uint64_t n_paths, size_t *bytes);
+
+/* Enqueue the whole estimate on opts->cuda_stream and return at once.
+ * d_workspace: device, >= heston_mc_workspace_bytes() bytes, 256-byte
+ * aligned, not used by another launch in flight.  d_out: device array of
+ * n_contracts x 12 doubles: out[c*12 + j] = mean of estimator j and
+ * out[c*12 + 6 + j] = its standard error, j in (price, delta, gamma, vega,
+ * rho, theta).  Validation as in heston_mc_price_greeks_ex; a CUDA launch
+ * failure returns HESTON_ERR_CUDA. */
+int heston_mc_launch(const heston_params *params, const heston_contract *contracts,
+                     uint32_t n_contracts, uint64_t n_paths, uint32_t n_steps,
+                     uint64_t rng_seed, const heston_options *opts,
+                     void *d_workspace, size_t workspace_bytes, double *d_out);
+
+/* ---- sharding: path-range partial sums and their reduction -------------- */
+
+/* Simulate global paths [path_begin, path_begin + n_paths) and write one
+ * partial-sum row per 64-path tile: d_tile_sums (device) holds
+ * ceil(n_paths / 64) rows of 12 * n_contracts doubles, row = (sum_x[6C],
+ * sum_x^2[6C]) with contract-major order.  path_begin must be a multiple
+ * of HESTON_TILE_PATHS.  Rows of consecutive shards concatenate into the
+ * rows of the unsharded range, so the reduction below gives bit-identical
+ * results for any split. */
+int heston_mc_launch_tiles(const heston_params *params, const heston_contract *contracts,
+                           uint32_t n_contracts, uint64_t path_begin, uint64_t n_paths,
+                           uint32_t n_steps, uint64_t rng_seed, const heston_options *opts,
+                           double *d_tile_sums);
+
+/* Reduce n_tiles rows of tile sums (device) over n_paths_total paths into
+ * d_out (device, n_contracts x 12 doubles as for heston_mc_launch), in a
+ * fixed order.  d_workspace: device scratch of at least
+ * heston_mc_workspace_bytes(n_contracts, n_paths_total) bytes (only its
+ * group-sum part is used).  stream: cudaStream_t or NULL. */
+int heston_mc_reduce_tiles(const double *d_tile_sums, uint64_t n_tiles, uint32_t n_contracts,
+                           uint64_t n_paths_total, void *d_workspace, size_t workspace_bytes,
+                           double *d_out, void *stream);
+
+/* ---- test support --------------------------------------------------------- */
+
+/* Per-path dump for `count` global path indices (host array `paths`):
+ * h_records (host, count x 15 doubles) receives X_N = ln(S_T/S0), V_N,
+ * dX_N/dv0, dV_N/dv0, dX_N/dT, dV_N/dT, sum S_ti, sum t_i S_ti,
+ * sum S_ti dX_ti/dv0, sum S_ti dX_ti/dT, the Gamma weights over all steps
+ * (sum u_k W_k, sum V_k+ dt) and over the steps before the first date,
+ * and min |V_k|; h_estimators (host, count x n_contracts x 6 doubles) the
+ * per-path estimators.  Synchronous; allocates device memory. */
+int heston_mc_debug_paths(const heston_params *params, const heston_contract *contracts,
+                          uint32_t n_contracts, uint32_t n_steps, uint64_t rng_seed,
+                          const heston_options *opts, const uint64_t *paths, uint32_t count,
+                          double *h_records, double *h_estimators);
+
+/* Raw random-number contract on the device, for tests: for each of `count`
+ * (path, step) pairs (host arrays) write the Philox words of the step's
+ * pair (4 x uint32, host h_words) and the step's (Za, Zb) in the chosen
+ * precision widened to double (host h_normals, 2 per entry). */
+int heston_rng_debug(uint64_t rng_seed, const uint64_t *paths, const uint32_t *steps,
+                     uint32_t count, int32_t prec, uint32_t *h_words, double *h_normals);
+
+/* Static description of a status code (never NULL). */
+const char *heston_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HESTON_MC_H */

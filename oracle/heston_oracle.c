@@ -151,7 +151,7 @@ typedef struct {
     double X, V, X_v, V_v, X_T, V_T;
     double sumS, sumtS, sumS_Xv, sumS_XT;   /* sum S_ti, sum t_i S_ti, sum S_ti X_v(t_i), sum S_ti X_T(t_i) */
     double GE, QE, GA, QA;
-    double minabsV;                         /* min |V_k| over k = 0..N (branch-flip classification) */
+    double minabsV;                         /* min |value deciding a truncation branch| (flip classification) */
 } orc_path;
 
 /* Number of doubles in orc_path, for the flat per-path dump. */
@@ -211,6 +211,7 @@ void orc_milstein_path(const orc_params *p, double T, uint32_t N, uint32_t M, in
 
         /* V step: V + kappa (theta - V) dt + xi sqrt(V dt) Z2 + xi^2 dt (Z2^2 - 1) / 4. */
         double Vn, Vn_v, Vn_T;
+        double branch;              /* the value whose sign picks the next branch */
         if (trunc == ORC_TRUNC_FULL) {
             /* Full truncation: the state keeps its sign; drift, diffusion and
              * the Milstein term (which comes from the diffusion) see V+. */
@@ -220,6 +221,7 @@ void orc_milstein_path(const orc_params *p, double T, uint32_t N, uint32_t M, in
             Vn_v = V_v - p->kappa * Vp_v * dt + p->xi * u_v * Z2;
             Vn_T = V_T + p->kappa * (p->theta - Vp) * ddt - p->kappa * Vp_T * dt
                    + p->xi * u_T * Z2 + 0.25 * p->xi * p->xi * ddt * (Z2 * Z2 - 1.0) * mil;
+            branch = Vn;
         } else {
             /* The paper's scheme as printed: update with V, then V = max(V, 0). */
             const double Vt = V + p->kappa * (p->theta - V) * dt + p->xi * u * Z2
@@ -231,11 +233,12 @@ void orc_milstein_path(const orc_params *p, double T, uint32_t N, uint32_t M, in
             Vn = keep ? Vt : 0.0;
             Vn_v = keep ? Vt_v : 0.0;
             Vn_T = keep ? Vt_T : 0.0;
+            branch = Vt;
         }
 
         X = Xn; X_v = Xn_v; X_T = Xn_T;
         V = Vn; V_v = Vn_v; V_T = Vn_T;
-        if (fabs(V) < minabsV) minabsV = fabs(V);
+        if (fabs(branch) < minabsV) minabsV = fabs(branch);
         if (traj_X) { traj_X[k + 1] = X; traj_V[k + 1] = V; }
 
         /* Asian monitoring date t_i = (k+1) dt when (k+1) is a multiple of the stride. */

@@ -1,0 +1,235 @@
+"""ctypes binding of ``libhestonmc.so`` (C ABI in ``include/heston_mc.h``).
+
+Argument marshalling only: every step of the path runs in the CUDA kernels of
+``csrc/heston_mc.cu``.  The functions keep the C names.  Device buffers may be
+given as ``torch.Tensor`` (CUDA) or raw integer addresses; streams as
+``torch.cuda.Stream`` or raw handles.  If the shared library has not been
+built, ``load()`` raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhestonmc.so")
+
+HESTON_OK = 0
+HESTON_WARN_GAMMA_UNDEFINED = 1
+HESTON_ERR_INVALID_ARG = -1
+HESTON_ERR_CUDA = -2
+HESTON_ERR_NOMEM = -3
+HESTON_ERR_TIMEOUT = -4
+HESTON_ERR_CANCELLED = -5
+HESTON_ERR_UNSUPPORTED = -6
+HESTON_ERR_WORKSPACE = -7
+HESTON_MAX_CONTRACTS = 8
+HESTON_TILE_PATHS = 64
+
+HESTON_EUROPEAN, HESTON_ASIAN_ARITH = 0, 1
+HESTON_TRUNC_FULL, HESTON_TRUNC_PAPER_FLOOR = 0, 1
+HESTON_RNG_PHILOX, HESTON_RNG_SOBOL_BB = 0, 1
+HESTON_FP32, HESTON_FP64 = 0, 1
+
+ESTIMATORS = ("price", "delta", "gamma", "vega", "rho", "theta")
+RECORD_FIELDS = ("X", "V", "X_v", "V_v", "X_T", "V_T", "sumS", "sumtS", "sumS_Xv", "sumS_XT",
+                 "GE", "QE", "GA", "QA", "minabsV")
+
+
+class heston_params(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("S0", "v0", "kappa", "theta", "xi", "rho", "r")]
+
+
+class heston_contract(ctypes.Structure):
+    _fields_ = [("payoff", ctypes.c_int32), ("is_put", ctypes.c_int32), ("K", ctypes.c_double),
+                ("T", ctypes.c_double), ("n_monitor", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
+
+
+class heston_options(ctypes.Structure):
+    _fields_ = [("trunc", ctypes.c_int32), ("rng", ctypes.c_int32), ("prec", ctypes.c_int32),
+                ("n_shifts", ctypes.c_uint32), ("cuda_stream", ctypes.c_void_p),
+                ("device", ctypes.c_int32), ("grid_ctas", ctypes.c_uint32),
+                ("block_threads", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+class heston_result(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ESTIMATORS] + [
+        ("se", ctypes.c_double * 6), ("n_paths", ctypes.c_uint64), ("status", ctypes.c_int32),
+        ("reserved", ctypes.c_int32)]
+
+
+class HestonError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+_lib = None
+
+
+def load():
+    """Load the in-tree CUDA library; raise if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: run __graft_entry__.build() "
+                           "(the CUDA path has no CPU fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.POINTER
+    u32, u64, i32, vp, sz = (ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32, ctypes.c_void_p,
+                             ctypes.c_size_t)
+    sig = {
+        "heston_mc_price_greeks": ([P(heston_params), P(heston_contract), u64, u32, u64,
+                                    P(heston_result)], i32),
+        "heston_mc_price_greeks_ex": ([P(heston_params), P(heston_contract), u32, u64, u32, u64,
+                                       P(heston_options), P(heston_result)], i32),
+        "heston_mc_workspace_bytes": ([u32, u64, P(sz)], i32),
+        "heston_mc_launch": ([P(heston_params), P(heston_contract), u32, u64, u32, u64,
+                              P(heston_options), vp, sz, vp], i32),
+        "heston_mc_launch_tiles": ([P(heston_params), P(heston_contract), u32, u64, u64, u32, u64,
+                                    P(heston_options), vp], i32),
+        "heston_mc_reduce_tiles": ([vp, u64, u32, u64, vp, sz, vp, vp], i32),
+        "heston_mc_debug_paths": ([P(heston_params), P(heston_contract), u32, u32, u64,
+                                   P(heston_options), P(u64), u32, P(ctypes.c_double),
+                                   P(ctypes.c_double)], i32),
+        "heston_rng_debug": ([u64, P(u64), P(u32), u32, i32, P(u32), P(ctypes.c_double)], i32),
+        "heston_status_string": ([ctypes.c_int], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def heston_status_string(status: int) -> str:
+    return load().heston_status_string(status).decode()
+
+
+def _check(rc: int) -> int:
+    if rc < 0:
+        raise HestonError(rc, heston_status_string(rc))
+    return rc
+
+
+def _ptr(x) -> int:
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "cuda_stream"):
+        return x.cuda_stream
+    raise TypeError(f"cannot take a device address of {type(x)}")
+
+
+def make_params(S0, v0, kappa, theta, xi, rho, r) -> heston_params:
+    return heston_params(S0, v0, kappa, theta, xi, rho, r)
+
+
+def make_contract(payoff, K, T, is_put=0, n_monitor=0) -> heston_contract:
+    return heston_contract(payoff, is_put, K, T, n_monitor, 0)
+
+
+def make_options(trunc=HESTON_TRUNC_FULL, prec=HESTON_FP64, stream=None, device=-1, grid_ctas=0,
+                 block_threads=0, rng=HESTON_RNG_PHILOX, n_shifts=0) -> heston_options:
+    return heston_options(trunc, rng, prec, n_shifts, _ptr(stream) or None, device, grid_ctas,
+                          block_threads, 0)
+
+
+def _contract_array(contracts):
+    arr = (heston_contract * len(contracts))()
+    for i, c in enumerate(contracts):
+        arr[i] = c
+    return arr
+
+
+def heston_mc_price_greeks(params: heston_params, contract: heston_contract, n_paths: int,
+                           n_steps: int, rng_seed: int) -> heston_result:
+    out = heston_result()
+    _check(load().heston_mc_price_greeks(ctypes.byref(params), ctypes.byref(contract), n_paths,
+                                         n_steps, rng_seed, ctypes.byref(out)))
+    return out
+
+
+def heston_mc_price_greeks_ex(params, contracts, n_paths, n_steps, rng_seed, options=None):
+    """Synchronous multi-contract call; returns a list of heston_result."""
+    cs = _contract_array(contracts)
+    out = (heston_result * len(contracts))()
+    opt = ctypes.byref(options) if options is not None else None
+    _check(load().heston_mc_price_greeks_ex(ctypes.byref(params), cs, len(contracts), n_paths,
+                                            n_steps, rng_seed, opt, out))
+    return list(out)
+
+
+def heston_mc_workspace_bytes(n_contracts: int, n_paths: int) -> int:
+    b = ctypes.c_size_t()
+    _check(load().heston_mc_workspace_bytes(n_contracts, n_paths, ctypes.byref(b)))
+    return b.value
+
+
+def heston_mc_launch(params, contracts, n_paths, n_steps, rng_seed, options, workspace,
+                     workspace_bytes, out) -> int:
+    """Asynchronous launch; ``workspace`` and ``out`` are device buffers."""
+    cs = _contract_array(contracts)
+    return _check(load().heston_mc_launch(ctypes.byref(params), cs, len(contracts), n_paths,
+                                          n_steps, rng_seed, ctypes.byref(options), _ptr(workspace),
+                                          workspace_bytes, _ptr(out)))
+
+
+def heston_mc_launch_tiles(params, contracts, path_begin, n_paths, n_steps, rng_seed, options,
+                           tile_sums) -> int:
+    cs = _contract_array(contracts)
+    return _check(load().heston_mc_launch_tiles(ctypes.byref(params), cs, len(contracts),
+                                                path_begin, n_paths, n_steps, rng_seed,
+                                                ctypes.byref(options), _ptr(tile_sums)))
+
+
+def heston_mc_reduce_tiles(tile_sums, n_tiles, n_contracts, n_paths_total, workspace,
+                           workspace_bytes, out, stream=None) -> int:
+    return _check(load().heston_mc_reduce_tiles(_ptr(tile_sums), n_tiles, n_contracts,
+                                                n_paths_total, _ptr(workspace), workspace_bytes,
+                                                _ptr(out), _ptr(stream) or None))
+
+
+def heston_mc_debug_paths(params, contracts, n_steps, rng_seed, options, paths):
+    """Per-path records (count, 15) and estimators (count, C, 6) as numpy arrays."""
+    paths = np.ascontiguousarray(np.asarray(paths, dtype=np.uint64))
+    n = len(paths)
+    rec = np.zeros((n, len(RECORD_FIELDS)))
+    est = np.zeros((n, len(contracts), 6))
+    cs = _contract_array(contracts)
+    D = ctypes.POINTER(ctypes.c_double)
+    _check(load().heston_mc_debug_paths(ctypes.byref(params), cs, len(contracts), n_steps,
+                                        rng_seed, ctypes.byref(options),
+                                        paths.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), n,
+                                        rec.ctypes.data_as(D), est.ctypes.data_as(D)))
+    return rec, est
+
+
+def heston_rng_debug(rng_seed, paths, steps, prec=HESTON_FP64):
+    """Philox words (count, 4) and normals (count, 2) computed on the device."""
+    paths = np.ascontiguousarray(np.asarray(paths, dtype=np.uint64))
+    steps = np.ascontiguousarray(np.asarray(steps, dtype=np.uint32))
+    n = len(paths)
+    words = np.zeros((n, 4), dtype=np.uint32)
+    normals = np.zeros((n, 2))
+    _check(load().heston_rng_debug(rng_seed,
+                                   paths.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                   steps.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), n, prec,
+                                   words.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
+                                   normals.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return words, normals
+
+
+def results_to_arrays(results):
+    """(C, 6) means and (C, 6) standard errors from a list of heston_result."""
+    m = np.array([[getattr(r, k) for k in ESTIMATORS] for r in results])
+    se = np.array([list(r.se) for r in results])
+    return m, se

@@ -1,0 +1,347 @@
+"""GPU path vs the FP64 CPU oracle, through the C ABI, on identical normals.
+
+Tolerances:
+  * random-number contract: Philox words bit-exact; FP64 normals within
+    1e-14; FP32 normals within 4e-6 * max(1, |z|).
+  * per path, FP64 path: every record field and estimator within 1e-9
+    relative (libm rounding only).
+  * per path, FP32 path: X_N, V_N and the payoff underlyings within 1e-5
+    relative (V relative to max(|V|, theta, v0)); paths whose truncation
+    branch or payoff indicator can flip between FP32 and FP64 (min |V_k| or
+    |A - K| within the FP32 error band) are counted, not compared, and must
+    stay below 1e-3 of the sample.
+  * estimates: FP64 within 1e-9 relative; FP32 within 3 standard errors and
+    within 1e-4 * max(1, |oracle|).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2309_10477_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+BASE = wl.BASE_PARAMS
+PAPER = wl.PAPER_PARAMS
+
+
+@pytest.fixture(scope="module")
+def nv(cuda_lib):
+    from paper_2309_10477_gb300 import native
+    return native
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    return torch
+
+
+def _gp(nv, d):
+    return nv.make_params(**d)
+
+
+def _gc(nv, cs):
+    return [nv.make_contract(*c) for c in cs]
+
+
+def _oc(cs):
+    return [oracle.Contract(c[0], c[1], c[2], c[3], c[4]) for c in cs]
+
+
+def _prec(nv, name):
+    return nv.HESTON_FP32 if name == "fp32" else nv.HESTON_FP64
+
+
+# ---------------------------------------------------------------------------
+# Random-number contract
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed", [42, 0, 2**64 - 1, 0x9E3779B97F4A7C15])
+def test_rng_contract(nv, seed):
+    rng = np.random.default_rng(1)
+    paths = np.concatenate([[0, 1, 63, 64, 2**32 - 1, 2**32, 2**40 + 7],
+                            rng.integers(0, 2**34, 2000)]).astype(np.uint64)
+    steps = np.concatenate([[0, 1, 2, 3, 251, 252, 99999],
+                            rng.integers(0, 600, 2000)]).astype(np.uint32)
+    w64, n64 = nv.heston_rng_debug(seed, paths, steps, nv.HESTON_FP64)
+    _, n32 = nv.heston_rng_debug(seed, paths, steps, nv.HESTON_FP32)
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    for i in range(len(paths)):
+        p, s = int(paths[i]), int(steps[i])
+        assert oracle.philox4x32_10([s // 2, p & 0xFFFFFFFF, p >> 32, 0], key) == list(w64[i])
+        za, zb = oracle.path_normals(seed, p, s + 1)
+        ref = np.array([za[s], zb[s]])
+        assert np.abs(n64[i] - ref).max() < 1e-14
+        assert (np.abs(n32[i] - ref) <= 4e-6 * np.maximum(1.0, np.abs(ref))).all()
+
+
+# ---------------------------------------------------------------------------
+# Per-path parity
+# ---------------------------------------------------------------------------
+
+CASES = [
+    ("base", BASE, 1), ("base", BASE, 2), ("base", BASE, 7), ("base", BASE, 64),
+    ("paper", PAPER, 3), ("paper", PAPER, 64), ("paper", PAPER, 128),
+]
+
+
+def _contracts_for(N):
+    return [(0, 100.0, 1.0, 0, 0), (1, 95.0, 1.0, 0, 0), (0, 105.0, 1.0, 1, 0),
+            (1, 100.0, 1.0, 1, 0)]
+
+
+def _paths():
+    return np.concatenate([np.arange(0, 700), 2**32 - 3 + np.arange(6),
+                           2**36 + 11 * np.arange(50)]).astype(np.uint64)
+
+
+@pytest.mark.parametrize("trunc", [0, 1])
+@pytest.mark.parametrize("name,params,N", CASES)
+def test_per_path_fp64(nv, name, params, N, trunc):
+    cs = _contracts_for(N)
+    paths = _paths()
+    rec_g, est_g = nv.heston_mc_debug_paths(_gp(nv, params), _gc(nv, cs), N, 42,
+                                            nv.make_options(trunc=trunc, prec=nv.HESTON_FP64), paths)
+    rec_o, est_o = oracle.debug_paths(oracle.Params(**params), _oc(cs), paths, N, 42, trunc)
+    scale = np.maximum(1.0, np.abs(rec_o[:, :14]))
+    bad = np.abs(rec_g[:, :14] - rec_o[:, :14]) > 1e-9 * scale
+    escale = np.maximum(1.0, np.abs(est_o))
+    bad_e = (np.abs(est_g - est_o) > 1e-9 * escale).any(axis=(1, 2))
+    bad_rows = bad.any(axis=1) | bad_e
+    # a truncation branch taken at |V| ~ 1e-16 may differ between libms
+    flips = bad_rows & (rec_o[:, 14] < 1e-12)
+    assert (bad_rows & ~flips).sum() == 0, np.nonzero(bad_rows & ~flips)[0][:5]
+    assert flips.sum() <= max(1, len(paths) // 1000)
+
+
+def _fp32_flip_mask(rec_o, est_o, cs, params, N, T=1.0):
+    """Paths whose FP32 run can take another branch than the FP64 oracle."""
+    near_zero = rec_o[:, 14] < 1e-5 * max(params["theta"], params["v0"])
+    S0 = params["S0"]
+    A_euro = S0 * np.exp(rec_o[:, 0])
+    near_k = np.zeros(len(rec_o), bool)
+    for c in cs:
+        M = c[4] or N
+        A = A_euro if c[0] == 0 else rec_o[:, 6] / M
+        near_k |= np.abs(A - c[1]) < 2e-5 * max(c[1], 1.0)
+    return near_zero | near_k
+
+
+@pytest.mark.parametrize("trunc", [0, 1])
+@pytest.mark.parametrize("name,params,N", CASES + [("base", BASE, 252)])
+def test_per_path_fp32(nv, name, params, N, trunc):
+    cs = _contracts_for(N)
+    paths = _paths()
+    rec_g, est_g = nv.heston_mc_debug_paths(_gp(nv, params), _gc(nv, cs), N, 42,
+                                            nv.make_options(trunc=trunc, prec=nv.HESTON_FP32), paths)
+    rec_o, est_o = oracle.debug_paths(oracle.Params(**params), _oc(cs), paths, N, 42, trunc)
+    flips = _fp32_flip_mask(rec_o, est_o, cs, params, N)
+    ok = ~flips
+    assert flips.sum() <= max(2, len(paths) // 1000)
+    X_g, X_o = rec_g[ok, 0], rec_o[ok, 0]
+    assert (np.abs(X_g - X_o) <= 1e-5 * np.maximum(1.0, np.abs(X_o))).all()
+    vscale = np.maximum(np.abs(rec_o[ok, 1]), max(params["theta"], params["v0"]))
+    assert (np.abs(rec_g[ok, 1] - rec_o[ok, 1]) <= 1e-5 * vscale).all()
+    # payoff underlyings S_T and Sbar (relative)
+    S0 = params["S0"]
+    for g, o in ((S0 * np.exp(X_g), S0 * np.exp(X_o)), (rec_g[ok, 6], rec_o[ok, 6])):
+        assert (np.abs(g - o) <= 1e-5 * np.abs(o)).all()
+    # discounted payoffs: absolute 1e-5 * max(K, A)
+    for ci, c in enumerate(cs):
+        A = np.maximum(c[1], np.abs(est_o[ok, ci, 1]) * S0)
+        assert (np.abs(est_g[ok, ci, 0] - est_o[ok, ci, 0]) <= 1e-5 * np.maximum(A, 1.0)).all()
+
+
+# ---------------------------------------------------------------------------
+# Estimates
+# ---------------------------------------------------------------------------
+
+def _gpu_estimates(nv, params, cs, n, N, seed, prec, trunc=0, **opt):
+    res = nv.heston_mc_price_greeks_ex(_gp(nv, params), _gc(nv, cs), n, N, seed,
+                                       nv.make_options(trunc=trunc, prec=prec, **opt))
+    return nv.results_to_arrays(res)
+
+
+@pytest.mark.parametrize("n", [2, 31, 33, 64, 65, 2381, (1 << 16) + 5])
+@pytest.mark.parametrize("N", [1, 3, 50])
+def test_estimates_fp64_match_oracle(nv, n, N):
+    cs = _contracts_for(N)
+    gm, gse = _gpu_estimates(nv, BASE, cs, n, N, 7, nv.HESTON_FP64)
+    om, ose = oracle.mc_price_greeks(oracle.Params(**BASE), _oc(cs), n, N, 7)
+    np.testing.assert_allclose(gm, om, rtol=1e-9, atol=1e-11)
+    # SE from (sum_x, sum_x^2) carries a rounding floor of about |mean| sqrt(eps / (n-1))
+    # (a constant estimator such as the European Rho with every path in the money)
+    floor = 1e-7 * np.maximum(1.0, np.abs(om))
+    assert (np.abs(gse - ose) <= 1e-6 * ose + floor).all()
+
+
+@pytest.mark.parametrize("trunc", [0, 1])
+@pytest.mark.parametrize("params", [BASE, PAPER], ids=["base", "paper"])
+def test_estimates_fp32_match_oracle(nv, params, trunc):
+    w = wl.multi_strike_fp32(1 << 16)
+    gm, gse = _gpu_estimates(nv, params, w.contracts, w.n_paths, w.n_steps, 3, nv.HESTON_FP32, trunc)
+    om, ose = oracle.mc_price_greeks(oracle.Params(**params), _oc(w.contracts), w.n_paths,
+                                     w.n_steps, 3, trunc)
+    d = np.abs(gm - om)
+    assert (d <= 3 * ose).all(), np.max(d / ose)
+    assert (d <= 1e-4 * np.maximum(1.0, np.abs(om))).all(), np.max(d / np.maximum(1, np.abs(om)))
+
+
+def test_single_european_fp64_full_size(nv):
+    """2^16 paths x 100 steps, FP64, one European call: the whole estimate."""
+    w = wl.single_european_fp64()
+    res = nv.heston_mc_price_greeks(_gp(nv, w.params), _gc(nv, w.contracts)[0], w.n_paths,
+                                    w.n_steps, w.seed)
+    gm, gse = nv.results_to_arrays([res])
+    om, ose = oracle.mc_price_greeks(oracle.Params(**w.params), _oc(w.contracts), w.n_paths,
+                                     w.n_steps, w.seed)
+    np.testing.assert_allclose(gm, om, rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(gse, ose, rtol=1e-6)
+    assert res.status == 0 and res.n_paths == w.n_paths
+
+
+def test_multi_strike_full_size_in_bench_launch(nv, torch_cuda):
+    """2^22 paths x 252 steps, 6 contracts, FP32: the launch bench.py times.
+    Sampled 64-path tile rows are checked against the oracle tile by tile,
+    and the full estimates against the oracle's full run."""
+    torch = torch_cuda
+    w = wl.multi_strike_fp32()
+    nc = len(w.contracts)
+    ws_bytes = nv.heston_mc_workspace_bytes(nc, w.n_paths)
+    ws = torch.empty(ws_bytes // 8 + 32, dtype=torch.float64, device="cuda")
+    off = (-ws.data_ptr()) % 256
+    base = ws.data_ptr() + off
+    out = torch.empty(nc * 12, dtype=torch.float64, device="cuda")
+    opts = nv.make_options(prec=nv.HESTON_FP32, stream=torch.cuda.current_stream())
+    nv.heston_mc_launch(_gp(nv, w.params), _gc(nv, w.contracts), w.n_paths, w.n_steps, w.seed,
+                        opts, base, ws_bytes - 0, out)
+    torch.cuda.synchronize()
+    n_tiles = w.n_paths // 64
+    rows = ws.view(torch.uint8)[off:off + n_tiles * 12 * nc * 8].view(torch.float64)
+    rows = rows.view(n_tiles, 12 * nc).cpu().numpy()
+    gout = out.cpu().numpy().reshape(nc, 12)
+
+    rng = np.random.default_rng(5)
+    sample = np.unique(np.concatenate([[0, 1, n_tiles - 1], rng.integers(0, n_tiles, 150)]))
+    P = oracle.Params(**w.params)
+    n_flip = 0
+    for t in sample:
+        s, s2 = oracle.mc_sums(P, _oc(w.contracts), 64, w.n_steps, w.seed, path_begin=int(t) * 64)
+        g, g2 = rows[t, :6 * nc].reshape(nc, 6), rows[t, 6 * nc:].reshape(nc, 6)
+        tol = 1e-5 * 64 * np.maximum(1.0, np.abs(s) / 64) + 1e-4 * np.abs(s)
+        if not (np.abs(g - s) <= tol).all():
+            # allowed only when a path of the tile sits on a branch point
+            rec, est = oracle.debug_paths(P, _oc(w.contracts), np.arange(t * 64, t * 64 + 64),
+                                          w.n_steps, w.seed)
+            assert _fp32_flip_mask(rec, est, w.contracts, w.params, w.n_steps).any(), t
+            n_flip += 1
+    assert n_flip <= 2
+
+    om, ose = oracle.mc_price_greeks(P, _oc(w.contracts), w.n_paths, w.n_steps, w.seed)
+    gm, gse = gout[:, :6], gout[:, 6:]
+    d = np.abs(gm - om)
+    assert (d <= 3 * ose).all()
+    assert (d <= 1e-4 * np.maximum(1.0, np.abs(om))).all()
+    np.testing.assert_allclose(gse, ose, rtol=1e-3)
+
+
+# ---------------------------------------------------------------------------
+# Determinism, sharding, launch shape, streams
+# ---------------------------------------------------------------------------
+
+def _launch(nv, torch, params, cs, n, N, seed, prec, **opt):
+    nc = len(cs)
+    ws_bytes = nv.heston_mc_workspace_bytes(nc, n)
+    ws = torch.empty(ws_bytes // 8, dtype=torch.float64, device="cuda")
+    out = torch.empty(nc * 12, dtype=torch.float64, device="cuda")
+    opts = nv.make_options(prec=prec, stream=torch.cuda.current_stream(), **opt)
+    nv.heston_mc_launch(_gp(nv, params), _gc(nv, cs), n, N, seed, opts, ws, ws_bytes, out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_launch_shape_and_repeat_do_not_change_bits(nv, torch_cuda, prec):
+    torch = torch_cuda
+    cs = _contracts_for(40)
+    n, N = 64 * 500 + 19, 40
+    p = _prec(nv, prec)
+    ref = _launch(nv, torch, BASE, cs, n, N, 9, p)
+    assert np.array_equal(ref, _launch(nv, torch, BASE, cs, n, N, 9, p))
+    for grid, block in ((1, 32), (7, 64), (300, 128), (0, 96)):
+        got = _launch(nv, torch, BASE, cs, n, N, 9, p, grid_ctas=grid, block_threads=block)
+        assert np.array_equal(ref, got), (grid, block)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_path_range_shards_reduce_to_identical_bits(nv, torch_cuda, prec):
+    torch = torch_cuda
+    cs = _contracts_for(30)
+    n, N, seed = 64 * 1000 + 17, 30, 11
+    p = _prec(nv, prec)
+    ref = _launch(nv, torch, BASE, cs, n, N, seed, p)
+    nc = len(cs)
+    n_tiles = -(-n // 64)
+    rows = torch.zeros(n_tiles * 12 * nc, dtype=torch.float64, device="cuda")
+    opts = nv.make_options(prec=p, stream=torch.cuda.current_stream())
+    bounds = [0, 64 * 300, 64 * 301, 64 * 700, n]
+    for lo, hi in zip(bounds[:-1], bounds[1:]):
+        view = rows[(lo // 64) * 12 * nc:]
+        nv.heston_mc_launch_tiles(_gp(nv, BASE), _gc(nv, cs), lo, hi - lo, N, seed, opts, view)
+    ws_bytes = nv.heston_mc_workspace_bytes(nc, n)
+    ws = torch.empty(ws_bytes // 8, dtype=torch.float64, device="cuda")
+    out = torch.empty(nc * 12, dtype=torch.float64, device="cuda")
+    nv.heston_mc_reduce_tiles(rows, n_tiles, nc, n, ws, ws_bytes, out,
+                              torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    assert np.array_equal(ref, out.cpu().numpy())
+
+
+def test_side_stream(nv, torch_cuda):
+    torch = torch_cuda
+    s = torch.cuda.Stream()
+    cs = _contracts_for(20)
+    with torch.cuda.stream(s):
+        got = _launch(nv, torch, BASE, cs, 5000, 20, 4, nv.HESTON_FP64)
+    om, ose = oracle.mc_price_greeks(oracle.Params(**BASE), _oc(cs), 5000, 20, 4)
+    np.testing.assert_allclose(got.reshape(len(cs), 12)[:, :6], om, rtol=1e-9, atol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Degenerate cases
+# ---------------------------------------------------------------------------
+
+def test_gamma_undefined_when_rho_is_one(nv):
+    p = dict(BASE, rho=-1.0)
+    cs = [(0, 100.0, 1.0, 0, 0)]
+    res = nv.heston_mc_price_greeks_ex(_gp(nv, p), _gc(nv, cs), 4096, 16, 1,
+                                       nv.make_options(prec=nv.HESTON_FP64))
+    assert res[0].status == nv.HESTON_WARN_GAMMA_UNDEFINED
+    gm, _ = nv.results_to_arrays(res)
+    om, _ = oracle.mc_price_greeks(oracle.Params(**p), _oc(cs), 4096, 16, 1)
+    assert math.isnan(gm[0, 2])
+    keep = [0, 1, 3, 4, 5]
+    np.testing.assert_allclose(gm[0, keep], om[0, keep], rtol=1e-9)
+
+
+@pytest.mark.parametrize("change", [dict(xi=0.0), dict(rho=0.0), dict(kappa=0.0),
+                                    dict(theta=0.0), dict(r=-0.01)])
+def test_degenerate_parameters(nv, change):
+    p = dict(BASE, **change)
+    cs = [(0, 100.0, 1.0, 0, 0), (1, 0.0, 1.0, 0, 5), (0, 0.0, 1.0, 1, 0)]
+    gm, _ = _gpu_estimates(nv, p, cs, 3000, 20, 5, nv.HESTON_FP64)
+    om, _ = oracle.mc_price_greeks(oracle.Params(**p), _oc(cs), 3000, 20, 5)
+    np.testing.assert_allclose(gm, om, rtol=1e-9, atol=1e-11)
+    # K = 0 put is worthless
+    assert (gm[2] == 0).all()
+
+
+def test_asian_with_sparse_dates_and_odd_steps(nv):
+    for N, M in ((9, 3), (128, 4), (7, 1), (7, 7)):
+        cs = [(1, 100.0, 1.0, 0, M), (1, 90.0, 1.0, 1, M), (0, 100.0, 1.0, 0, 0)]
+        gm, _ = _gpu_estimates(nv, PAPER, cs, 2000, N, 2, nv.HESTON_FP64)
+        om, _ = oracle.mc_price_greeks(oracle.Params(**PAPER), _oc(cs), 2000, N, 2)
+        np.testing.assert_allclose(gm, om, rtol=1e-9, atol=1e-11)
