@@ -50,10 +50,10 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, PhiloxKey key)
     uint32_t k0 = key.k0, k1 = key.k1;
 #pragma unroll
     for (int i = 0; i < 10; ++i) {
-        const uint32_t lo0 = 0xD2511F53u * c.x;
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
-        const uint32_t lo1 = 0xCD9E8D57u * c.z;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        const unsigned long long p0 = (unsigned long long)c.x * 0xD2511F53u;
+        const unsigned long long p1 = (unsigned long long)c.z * 0xCD9E8D57u;
+        const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
         c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
         k0 += 0x9E3779B9u;
         k1 += 0xBB67AE85u;
@@ -66,15 +66,27 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, PhiloxKey key)
 // u2 = (b>>8) 2^-24 in [0,1); Za = sqrt(-2 ln u1) cos 2 pi u2,
 // Zb = sqrt(-2 ln u1) sin 2 pi u2.  The uniforms are exact in both precisions.
 // ---------------------------------------------------------------------------
+// FP32 special-function unit approximations (PTX .approx forms).  Documented
+// bounds: sin/cos absolute error about 2^-20.9 on [-pi, pi]; ex2, rsqrt,
+// sqrt relative error about 2^-22.  ln u1 keeps the accurate logf: the
+// radius sqrt(-2 ln u1) needs ln u1 to full relative accuracy as u1 -> 1,
+// where lg2.approx's absolute error would dominate.
+__device__ __forceinline__ float sin_approx(float x) { float y; asm("sin.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x)); return y; }
+__device__ __forceinline__ float cos_approx(float x) { float y; asm("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x)); return y; }
+__device__ __forceinline__ float ex2_approx(float x) { float y; asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x)); return y; }
+__device__ __forceinline__ float sqrt_approx(float x) { float y; asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x)); return y; }
+__device__ __forceinline__ float rsqrt_approx(float x) { float y; asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x)); return y; }
+
 __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float &za, float &zb)
 {
-    const float u1 = (float)((a >> 8) + 1u) * 5.9604644775390625e-8f;
-    const float u2 = (float)(b >> 8) * 5.9604644775390625e-8f;
-    const float rad = sqrtf(-2.0f * logf(u1));
-    float s, c;
-    sincospif(2.0f * u2, &s, &c);
-    za = rad * c;
-    zb = rad * s;
+    // u1 = (a>>8) 2^-24 + 2^-24: the top 24 bits convert exactly.
+    const float u1 = fmaf((float)(a & 0xFFFFFF00u), 2.3283064365386963e-10f, 5.9604644775390625e-8f);
+    // The top 24 bits of b read as a signed 32-bit integer are 2^32 (u2 - [u2 >= 1/2]),
+    // so the angle 2 pi u2 lands in [-pi, pi) with the same sine and cosine.
+    const float ang = (float)(int32_t)(b & 0xFFFFFF00u) * 1.4629180792671596e-9f;   // 2 pi / 2^32
+    const float rad = sqrt_approx(-2.0f * logf(u1));
+    za = rad * cos_approx(ang);
+    zb = rad * sin_approx(ang);
 }
 
 __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, double &za, double &zb)
@@ -88,9 +100,9 @@ __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, double &za, d
     zb = rad * s;
 }
 
-__device__ __forceinline__ float rsqrt_pos(float y) { return y > 0.0f ? rsqrtf(y) : 0.0f; }
+__device__ __forceinline__ float rsqrt_pos(float y) { return y > 0.0f ? rsqrt_approx(y) : 0.0f; }
 __device__ __forceinline__ double rsqrt_pos(double y) { return y > 0.0 ? rsqrt(y) : 0.0; }
-__device__ __forceinline__ float exp_r(float x) { return expf(x); }
+__device__ __forceinline__ float exp_r(float x) { return ex2_approx(x * 1.44269504f); }
 __device__ __forceinline__ double exp_r(double x) { return exp(x); }
 
 // ---------------------------------------------------------------------------
@@ -146,8 +158,39 @@ __device__ __forceinline__ void init_state(PathState<R> &s, R v0)
 }
 
 // One Milstein step with its tangents, from independent normals (za, zb).
+// FP32 full truncation: the same recursion with shared products hoisted
+// (xi Z2 feeds V and both V tangents; the truncation mask scales 1/(2u)).
+__device__ __forceinline__ void milstein_step_f32_full(PathState<float> &s, float za, float zb,
+                                                       const Coef<float> &k)
+{
+    const float Z2 = fmaf(k.rho, za, k.sq * zb);
+    const float W = fmaf(k.sq, za, -k.rho * zb);
+    const float xZ2 = k.xi * Z2;
+    const bool pos = s.V > 0.0f;
+    const float Vp = fmaxf(s.V, 0.0f);
+    const float Vpv = pos ? s.Vv : 0.0f;
+    const float VpT = pos ? s.VT : 0.0f;
+    const float y = Vp * k.dt;                                  // V+ dt
+    const float rs = rsqrt_approx(fmaxf(y, 1e-30f));            // finite at y = 0
+    const float u = y * rs;                                     // sqrt(V+ dt), 0 at 0
+    const float hdt = 0.5f * k.dt * rs;                         // dt / (2u)
+    const float uv = Vpv * hdt;                                 // du/dv0
+    const float uT = fmaf(VpT, hdt, Vp * (0.5f * k.ddt * rs));  // du/dT
+    s.GE = fmaf(u, W, s.GE);
+    s.QE += y;
+    const float drift = fmaf(-0.5f, Vp, k.r);
+    s.X = fmaf(u, za, fmaf(drift, k.dt, s.X));
+    s.Xv = fmaf(uv, za, fmaf(-k.half_dt, Vpv, s.Xv));
+    s.XT = fmaf(uT, za, fmaf(-k.half_dt, VpT, fmaf(drift, k.ddt, s.XT)));
+    const float z2m1 = fmaf(Z2, Z2, -1.0f);
+    const float c4 = pos ? k.c4 : 0.0f, c4T = pos ? k.c4T : 0.0f;
+    s.V = fmaf(c4, z2m1, fmaf(xZ2, u, fmaf(-k.kdt, Vp, s.V + k.kth_dt)));
+    s.Vv = fmaf(xZ2, uv, fmaf(-k.kdt, Vpv, s.Vv));
+    s.VT = fmaf(c4T, z2m1, fmaf(xZ2, uT, fmaf(-k.kdt, VpT, fmaf(-k.kappa_ddt, Vp, s.VT + k.kth_ddt))));
+}
+
 template <typename R, int TRUNC>
-__device__ __forceinline__ void milstein_step(PathState<R> &s, R za, R zb, const Coef<R> &k)
+__device__ __forceinline__ void milstein_step_generic(PathState<R> &s, R za, R zb, const Coef<R> &k)
 {
     const R Z1 = za;
     const R Z2 = k.rho * za + k.sq * zb;
@@ -190,6 +233,15 @@ __device__ __forceinline__ void milstein_step(PathState<R> &s, R za, R zb, const
         s.Vv = keep ? Vtv : R(0);
         s.VT = keep ? VtT : R(0);
     }
+}
+
+template <typename R, int TRUNC>
+__device__ __forceinline__ void milstein_step(PathState<R> &s, R za, R zb, const Coef<R> &k)
+{
+    if constexpr (sizeof(R) == 4 && TRUNC == HESTON_TRUNC_FULL)
+        milstein_step_f32_full(s, za, zb, k);
+    else
+        milstein_step_generic<R, TRUNC>(s, za, zb, k);
 }
 
 // Asian monitoring date after step index kp1 (= k + 1).
@@ -255,9 +307,12 @@ __device__ __forceinline__ R warp_sum(R v)
     return v;
 }
 
+// Asian monitoring layout: none, a date after every step, or every `stride` steps.
+enum { MON_NONE = 0, MON_EVERY = 1, MON_STRIDE = 2 };
+
 // Run NP paths (one lane) through all N steps.  Step k uses Philox counter
 // (k/2, path_lo, path_hi, 0): words (x, y) for even k, (z, w) for odd k.
-template <typename R, int TRUNC, bool ASIAN, int NP>
+template <typename R, int TRUNC, int MON, int NP>
 __device__ __forceinline__ void simulate(PathState<R> (&s)[NP], const uint32_t (&plo)[NP],
                                          const uint32_t (&phi)[NP], const Coef<R> &k,
                                          const ContractSet &cs, PhiloxKey key, uint32_t N)
@@ -280,8 +335,12 @@ __device__ __forceinline__ void simulate(PathState<R> (&s)[NP], const uint32_t (
                 else        box_muller(w[q].z, w[q].w, za, zb);
                 milstein_step<R, TRUNC>(s[q], za, zb, k);
             }
-            if (ASIAN) {
-                const uint32_t kp1 = 2u * j + 1u + (uint32_t)h;
+            const uint32_t kp1 = 2u * j + 1u + (uint32_t)h;
+            if (MON == MON_EVERY) {
+                const bool first = (h == 0) && (j == 0);
+#pragma unroll
+                for (int q = 0; q < NP; ++q) monitor(s[q], R(kp1), first);
+            } else if (MON == MON_STRIDE) {
                 if (kp1 == next_mon) {
 #pragma unroll
                     for (int q = 0; q < NP; ++q) monitor(s[q], R(kp1), kp1 == stride);
@@ -298,7 +357,7 @@ __device__ __forceinline__ void simulate(PathState<R> (&s)[NP], const uint32_t (
             box_muller(w.x, w.y, za, zb);
             milstein_step<R, TRUNC>(s[q], za, zb, k);
         }
-        if (ASIAN && N == next_mon) {
+        if (MON == MON_EVERY || (MON == MON_STRIDE && N == next_mon)) {
 #pragma unroll
             for (int q = 0; q < NP; ++q) monitor(s[q], R(N), N == stride);
         }
@@ -311,7 +370,7 @@ __device__ __forceinline__ void simulate(PathState<R> (&s)[NP], const uint32_t (
 // sum_x and sum_x^2 (the lane's two paths added first, then a fixed xor
 // butterfly), so tile rows do not depend on the launch shape.
 // ---------------------------------------------------------------------------
-template <typename R, int TRUNC, bool ASIAN>
+template <typename R, int TRUNC, int MON>
 __global__ void __launch_bounds__(kPathBlock) heston_paths_kernel(Coef<R> k, ContractSet cs, Launch a)
 {
     const int lane = threadIdx.x & 31;
@@ -331,7 +390,7 @@ __global__ void __launch_bounds__(kPathBlock) heston_paths_kernel(Coef<R> k, Con
             plo[q] = (uint32_t)g;
             phi[q] = (uint32_t)(g >> 32);
         }
-        simulate<R, TRUNC, ASIAN, 2>(s, plo, phi, k, cs, a.key, a.N);
+        simulate<R, TRUNC, MON, 2>(s, plo, phi, k, cs, a.key, a.N);
 
         R eT[2];
 #pragma unroll
@@ -355,7 +414,7 @@ __global__ void __launch_bounds__(kPathBlock) heston_paths_kernel(Coef<R> k, Con
 
 // Test kernel: one thread per requested path, the same step code, writes the
 // per-path record and estimators.
-template <typename R, int TRUNC, bool ASIAN>
+template <typename R, int TRUNC, int MON>
 __global__ void heston_debug_kernel(Coef<R> k, ContractSet cs, PhiloxKey key, uint32_t N,
                                     const uint64_t *paths, uint32_t count, double *rec, double *est)
 {
@@ -364,7 +423,7 @@ __global__ void heston_debug_kernel(Coef<R> k, ContractSet cs, PhiloxKey key, ui
     const uint64_t g = paths[i];
     PathState<R> s[1];
     const uint32_t plo[1] = {(uint32_t)g}, phi[1] = {(uint32_t)(g >> 32)};
-    simulate<R, TRUNC, ASIAN, 1>(s, plo, phi, k, cs, key, N);
+    simulate<R, TRUNC, MON, 1>(s, plo, phi, k, cs, key, N);
     const R eT = exp_r(s[0].X);
     const double S0 = cs.S0;
     double *o = rec + (uint64_t)i * kRecordDoubles;
@@ -580,10 +639,10 @@ size_t workspace_bytes(uint32_t nc, uint64_t n_paths)
     return align256(nt * w) + align256(groups_for(nt) * w);
 }
 
-template <typename R, int TRUNC, bool ASIAN>
+template <typename R, int TRUNC, int MON>
 cudaError_t launch_paths_t(const Prepared &pp, const Coef<R> &k, const Launch &a, cudaStream_t st)
 {
-    auto kern = heston_paths_kernel<R, TRUNC, ASIAN>;
+    auto kern = heston_paths_kernel<R, TRUNC, MON>;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -609,20 +668,30 @@ cudaError_t launch_paths_t(const Prepared &pp, const Coef<R> &k, const Launch &a
     return cudaGetLastError();
 }
 
+int mon_mode(const ContractSet &cs)
+{
+    if (!cs.has_asian) return MON_NONE;
+    return cs.stride == 1 ? MON_EVERY : MON_STRIDE;
+}
+
+template <typename R>
+cudaError_t launch_paths_r(const Prepared &pp, const Coef<R> &k, const Launch &a, cudaStream_t st)
+{
+    const int mon = mon_mode(pp.cs);
+    if (pp.opt.trunc == HESTON_TRUNC_FULL) {
+        if (mon == MON_NONE) return launch_paths_t<R, 0, MON_NONE>(pp, k, a, st);
+        if (mon == MON_EVERY) return launch_paths_t<R, 0, MON_EVERY>(pp, k, a, st);
+        return launch_paths_t<R, 0, MON_STRIDE>(pp, k, a, st);
+    }
+    if (mon == MON_NONE) return launch_paths_t<R, 1, MON_NONE>(pp, k, a, st);
+    if (mon == MON_EVERY) return launch_paths_t<R, 1, MON_EVERY>(pp, k, a, st);
+    return launch_paths_t<R, 1, MON_STRIDE>(pp, k, a, st);
+}
+
 cudaError_t launch_paths(const Prepared &pp, const Launch &a, cudaStream_t st)
 {
-    const bool asian = pp.cs.has_asian != 0;
-    const bool full = pp.opt.trunc == HESTON_TRUNC_FULL;
-    if (pp.opt.prec == HESTON_FP32) {
-        if (full) return asian ? launch_paths_t<float, 0, true>(pp, pp.kf, a, st)
-                               : launch_paths_t<float, 0, false>(pp, pp.kf, a, st);
-        return asian ? launch_paths_t<float, 1, true>(pp, pp.kf, a, st)
-                     : launch_paths_t<float, 1, false>(pp, pp.kf, a, st);
-    }
-    if (full) return asian ? launch_paths_t<double, 0, true>(pp, pp.kd, a, st)
-                           : launch_paths_t<double, 0, false>(pp, pp.kd, a, st);
-    return asian ? launch_paths_t<double, 1, true>(pp, pp.kd, a, st)
-                 : launch_paths_t<double, 1, false>(pp, pp.kd, a, st);
+    if (pp.opt.prec == HESTON_FP32) return launch_paths_r<float>(pp, pp.kf, a, st);
+    return launch_paths_r<double>(pp, pp.kd, a, st);
 }
 
 cudaError_t launch_reduce(const double *tile_sums, uint64_t n_tiles, int nc, uint64_t n_paths,
@@ -836,16 +905,18 @@ int heston_mc_debug_paths(const heston_params *params, const heston_contract *co
     if (e == HESTON_OK) {
         const unsigned grid = (count + 127) / 128;
         const PhiloxKey key = key_of(rng_seed);
-        const bool asian = pp.cs.has_asian != 0;
+        const int mon = mon_mode(pp.cs);
         const bool full = pp.opt.trunc == HESTON_TRUNC_FULL;
-#define HESTON_DBG(R, TR, AS, K) heston_debug_kernel<R, TR, AS><<<grid, 128, 0, st>>>(K, pp.cs, key, pp.N, dp, count, dr, de)
+#define HESTON_DBG(R, TR, MO, K) heston_debug_kernel<R, TR, MO><<<grid, 128, 0, st>>>(K, pp.cs, key, pp.N, dp, count, dr, de)
+#define HESTON_DBG_M(R, TR, K) do { if (mon == MON_NONE) HESTON_DBG(R, TR, MON_NONE, K); \
+                                    else if (mon == MON_EVERY) HESTON_DBG(R, TR, MON_EVERY, K); \
+                                    else HESTON_DBG(R, TR, MON_STRIDE, K); } while (0)
         if (pp.opt.prec == HESTON_FP32) {
-            if (full) { if (asian) HESTON_DBG(float, 0, true, pp.kf); else HESTON_DBG(float, 0, false, pp.kf); }
-            else      { if (asian) HESTON_DBG(float, 1, true, pp.kf); else HESTON_DBG(float, 1, false, pp.kf); }
+            if (full) HESTON_DBG_M(float, 0, pp.kf); else HESTON_DBG_M(float, 1, pp.kf);
         } else {
-            if (full) { if (asian) HESTON_DBG(double, 0, true, pp.kd); else HESTON_DBG(double, 0, false, pp.kd); }
-            else      { if (asian) HESTON_DBG(double, 1, true, pp.kd); else HESTON_DBG(double, 1, false, pp.kd); }
+            if (full) HESTON_DBG_M(double, 0, pp.kd); else HESTON_DBG_M(double, 1, pp.kd);
         }
+#undef HESTON_DBG_M
 #undef HESTON_DBG
         if (cudaGetLastError() != cudaSuccess) e = HESTON_ERR_CUDA;
     }
