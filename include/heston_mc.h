@@ -1,13 +1,13 @@
 /*
  * heston_mc.h -- C ABI of the GB300 Monte Carlo Heston pricer (arXiv 2309.10477).
  *
- * The library simulates Heston paths (Eq. heston_eq, Sec. 2.3) with the
+ * The library simulates Heston paths (Eq. heston_eq, Sec. 2.1) with the
  * Milstein scheme for ln S and V (Sec. 2.4.2, Algorithm "Milstein
  * approximation under Heston model"), driven by correlated normals
  * (Algorithm "Generation of two correlated Normal random variables"), and
  * returns Monte Carlo estimates (Algorithm "Monte Carlo option pricing
  * estimation", Sec. 2.5) of the discounted price and the Greeks Delta,
- * Gamma, Vega, Rho and Theta (named in Sec. 2.2; pathwise Delta and Rho of
+ * Gamma, Vega, Rho and Theta (named in Sec. 2; pathwise Delta and Rho of
  * Eq. euro_pw and Eq. asian_pw) with their standard errors, all from the
  * same paths.  Every path lives in registers on the GPU; nothing per path
  * is written to memory.
@@ -69,7 +69,7 @@ typedef enum { HESTON_EUROPEAN = 0, HESTON_ASIAN_ARITH = 1 } heston_payoff;
 
 /* One option.  European payoff max(S_T - K, 0) (put: max(K - S_T, 0));
  * arithmetic Asian payoff on Sbar = (1/M) sum_{i=1..M} S_{t_i} with equal
- * dates t_i = i T / M (Sec. 2.1).  n_monitor = M; 0 means M = n_steps;
+ * dates t_i = i T / M (Sec. 2).  n_monitor = M; 0 means M = n_steps;
  * n_steps must be a multiple of M. */
 typedef struct {
     int32_t payoff;      /* heston_payoff */

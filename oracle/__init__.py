@@ -10,9 +10,6 @@ Contents:
     per-path estimators and the Monte Carlo driver of Sec. 2.5 (plain C, FP64).
   * ``closed_form`` -- Black-Scholes and the Heston characteristic-function
     price and Greeks (the "real price" the paper quotes in Sec. 3).
-  * ``exact`` -- Broadie-Kaya exact simulation (Sec. 2.3).
-  * ``sobol`` -- Sobol points, Brownian bridge and digital shifts for the
-    quasi-Monte Carlo variant (Sec. 2.7).
 
 Parity pins live in ``tests/test_oracle_*.py``; functions with no pin say
 "parity unpinned" in their docstring.

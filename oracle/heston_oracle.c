@@ -22,10 +22,10 @@
  *     floor max(V, 0) after each update.
  *   - The Monte Carlo estimator of the Algorithm "Monte Carlo option pricing
  *     estimation" (Sec. 2.5), extended to the pathwise Greeks of
- *     Eq. (euro_pw) and Eq. (asian_pw) (Sec. 2.2.1).  Asian Rho uses the
+ *     Eq. (euro_pw) and Eq. (asian_pw) (pathwise method, Sec. 2).  Asian Rho uses the
  *     derivative of the Asian payoff (the printed K*T prefactor is dropped;
  *     with one monitoring date it then reduces to the European Rho).
- *   - Gamma, Vega and Theta, which the paper only names (Sec. 2.2): Gamma by
+ *   - Gamma, Vega and Theta, which the paper only names (Sec. 2): Gamma by
  *     a pathwise / likelihood-ratio mix on the same paths, Vega = dV/dv0 and
  *     Theta = -dV/dT by pathwise tangent recursions.
  *

@@ -2,7 +2,7 @@
 // Greeks, behind the C ABI declared in include/heston_mc.h.
 //
 // Method (arXiv 2309.10477):
-//   * Heston dynamics, Eq. (heston_eq), Sec. 2.3.
+//   * Heston dynamics, Eq. (heston_eq), Sec. 2.1.
 //   * Correlated normals, Algorithm "Generation of two correlated Normal
 //     random variables" (Sec. 2.4.1): Z1 = Za, Z2 = rho Z1 + sqrt(1-rho^2) Zb.
 //   * Milstein for ln S and V (Sec. 2.4.2): ln S += (r - V/2) dt + sqrt(V dt) Z1
@@ -11,7 +11,7 @@
 //   * Monte Carlo average (Algorithm "Monte Carlo option pricing estimation",
 //     Sec. 2.5) of the discounted payoff and of the pathwise Greeks of
 //     Eq. (euro_pw) / Eq. (asian_pw); Gamma, Vega (d/dv0) and Theta (-d/dT),
-//     which the paper only names (Sec. 2.2), come from a pathwise /
+//     which the paper only names (Sec. 2), come from a pathwise /
 //     likelihood-ratio Gamma weight and tangent recursions run alongside
 //     the path.
 //
@@ -67,14 +67,13 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, PhiloxKey key)
 // Zb = sqrt(-2 ln u1) sin 2 pi u2.  The uniforms are exact in both precisions.
 // ---------------------------------------------------------------------------
 // FP32 special-function unit approximations (PTX .approx forms).  Documented
-// bounds: sin/cos absolute error about 2^-20.9 on [-pi, pi]; ex2, rsqrt,
-// sqrt relative error about 2^-22.  ln u1 keeps the accurate logf: the
-// radius sqrt(-2 ln u1) needs ln u1 to full relative accuracy as u1 -> 1,
-// where lg2.approx's absolute error would dominate.
+// bounds: sin/cos absolute error about 2^-20.9 on [-pi, pi]; lg2 absolute
+// error about 2^-22; ex2, rsqrt, sqrt relative error about 2^-22.
 __device__ __forceinline__ float sin_approx(float x) { float y; asm("sin.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x)); return y; }
 __device__ __forceinline__ float cos_approx(float x) { float y; asm("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x)); return y; }
 __device__ __forceinline__ float ex2_approx(float x) { float y; asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x)); return y; }
 __device__ __forceinline__ float sqrt_approx(float x) { float y; asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x)); return y; }
+__device__ __forceinline__ float lg2_approx(float x) { float y; asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x)); return y; }
 __device__ __forceinline__ float rsqrt_approx(float x) { float y; asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x)); return y; }
 
 __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float &za, float &zb)
@@ -84,7 +83,22 @@ __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float &za, fl
     // The top 24 bits of b read as a signed 32-bit integer are 2^32 (u2 - [u2 >= 1/2]),
     // so the angle 2 pi u2 lands in [-pi, pi) with the same sine and cosine.
     const float ang = (float)(int32_t)(b & 0xFFFFFF00u) * 1.4629180792671596e-9f;   // 2 pi / 2^32
-    const float rad = sqrt_approx(-2.0f * logf(u1));
+    // r2 = -2 ln u1.  For u1 <= 0.9 from lg2.approx, whose absolute error
+    // (2 ln2 2^-22 in r2) is below 1.6e-6 of r2 >= 0.21.  Near 1, where that
+    // absolute error would swamp the small radius, from the series
+    // -2 ln(1 - w) = 2 sum_k w^k / k in w = 1 - u1 (exact), truncated after
+    // w^7 (relative error < 1.4e-8 at w = 0.1).  Both are evaluated and one
+    // selected: lanes of a warp fall on both sides.
+    const float w = 1.0f - u1;
+    const float r2_far = -1.3862943611198906f * lg2_approx(u1);
+    float p = fmaf(w, 0.2857142857f, 0.3333333333f);
+    p = fmaf(w, p, 0.4f);
+    p = fmaf(w, p, 0.5f);
+    p = fmaf(w, p, 0.6666666667f);
+    p = fmaf(w, p, 1.0f);
+    p = fmaf(w, p, 2.0f);
+    const float r2 = u1 > 0.9f ? w * p : r2_far;
+    const float rad = sqrt_approx(r2);
     za = rad * cos_approx(ang);
     zb = rad * sin_approx(ang);
 }
@@ -117,15 +131,22 @@ struct Coef {
     R rho, sq;                    // sq = sqrt(1 - rho^2)
 };
 
-// Contracts priced on the shared paths (all with the same T and Asian M).
+// Contracts priced on the shared paths (all with the same T and Asian M),
+// with their constants rounded once on the host to the path precision.
+template <typename R>
 struct ContractSet {
     int32_t n;
     int32_t has_asian;
     uint32_t M, stride;           // Asian dates and steps between them
     int32_t payoff[kMaxC];
     int32_t is_put[kMaxC];
-    double K[kMaxC];
-    double T, D, S0, r, sq;       // D = exp(-rT)
+    R K[kMaxC];
+    R T, D, r;                    // D = exp(-rT)
+    R S0, inv_S0, inv_S0sq;
+    R inv_sq;                     // 1 / sqrt(1 - rho^2)
+    R S0_over_M;                  // S0 / M
+    R dAr_scale;                  // S0 T / M^2: d Sbar / dr = dAr_scale ((M+1) sA - sC)
+    R Mp1;                        // M + 1
 };
 
 struct Launch {
@@ -138,14 +159,15 @@ struct Launch {
 };
 
 // Registers of one path.  X = ln(S/S0); *_v = d/dv0, *_T = d/dT tangents.
-// sA = sum_i e^{X(t_i)}, sB = sum_i (step index of t_i) e^{X(t_i)},
+// Over the dates i = 1..M: sA = sum_i e^{X(t_i)} (running), sC = sum of the
+// running sA after each date, so that sum_i i e^{X(t_i)} = (M+1) sA - sC;
 // sAv / sAT = sum_i e^{X(t_i)} X_v(t_i) / X_T(t_i).  GE/QE: Gamma weights
 // sum_k u_k W_k and sum_k V_k+ dt over all steps; GA/QA: the same over the
 // steps before the first monitoring date.
 template <typename R>
 struct PathState {
     R X, V, Xv, Vv, XT, VT;
-    R sA, sB, sAv, sAT;
+    R sA, sC, sAv, sAT;
     R GE, QE, GA, QA;
 };
 
@@ -153,7 +175,7 @@ template <typename R>
 __device__ __forceinline__ void init_state(PathState<R> &s, R v0)
 {
     s.X = R(0); s.V = v0; s.Xv = R(0); s.Vv = R(1); s.XT = R(0); s.VT = R(0);
-    s.sA = R(0); s.sB = R(0); s.sAv = R(0); s.sAT = R(0);
+    s.sA = R(0); s.sC = R(0); s.sAv = R(0); s.sAT = R(0);
     s.GE = R(0); s.QE = R(0); s.GA = R(0); s.QA = R(0);
 }
 
@@ -244,13 +266,14 @@ __device__ __forceinline__ void milstein_step(PathState<R> &s, R za, R zb, const
         milstein_step_generic<R, TRUNC>(s, za, zb, k);
 }
 
-// Asian monitoring date after step index kp1 (= k + 1).
+// Asian monitoring date (first: the first date, which closes the Asian
+// Gamma weight window).
 template <typename R>
-__device__ __forceinline__ void monitor(PathState<R> &s, R kp1, bool first)
+__device__ __forceinline__ void monitor(PathState<R> &s, bool first)
 {
     const R e = exp_r(s.X);
     s.sA += e;
-    s.sB += kp1 * e;
+    s.sC += s.sA;
     s.sAv += e * s.Xv;
     s.sAT += e * s.XT;
     if (first) { s.GA = s.GE; s.QA = s.QE; }
@@ -263,24 +286,24 @@ __device__ __forceinline__ void monitor(PathState<R> &s, R kp1, bool first)
 //   vega = D phi' dA/dv0; rho = -T price + D phi' dA/dr; theta = r price - D phi' dA/dT.
 // For the European call rho reduces to D K T 1{S_T > K} (Eq. euro_pw).
 template <typename R>
-__device__ __forceinline__ void estimators(const PathState<R> &s, const ContractSet &cs, int c,
-                                           R eT, R dt, R est[6])
+__device__ __forceinline__ void estimators(const PathState<R> &s, const ContractSet<R> &cs, int c,
+                                           R eT, R est[6])
 {
-    const R S0 = R(cs.S0), K = R(cs.K[c]), D = R(cs.D), T = R(cs.T), r = R(cs.r);
+    const R K = cs.K[c], D = cs.D, T = cs.T;
+    const bool euro = cs.payoff[c] == HESTON_EUROPEAN;
     R A, dAv, dAT, dAr, lr;
-    if (cs.payoff[c] == HESTON_EUROPEAN) {
-        A = S0 * eT;
+    if (euro) {
+        A = cs.S0 * eT;
         dAv = A * s.Xv;
         dAT = A * s.XT;
         dAr = T * A;
-        lr = s.GE / (R(cs.sq) * s.QE);
+        lr = s.GE * cs.inv_sq / s.QE;
     } else {
-        const R sc = S0 / R(cs.M);
-        A = sc * s.sA;
-        dAv = sc * s.sAv;
-        dAT = sc * s.sAT;
-        dAr = sc * dt * s.sB;
-        lr = s.GA / (R(cs.sq) * s.QA);
+        A = cs.S0_over_M * s.sA;
+        dAv = cs.S0_over_M * s.sAv;
+        dAT = cs.S0_over_M * s.sAT;
+        dAr = cs.dAr_scale * (cs.Mp1 * s.sA - s.sC);
+        lr = s.GA * cs.inv_sq / s.QA;
     }
     R pay, slope;
     if (!cs.is_put[c]) {
@@ -292,11 +315,11 @@ __device__ __forceinline__ void estimators(const PathState<R> &s, const Contract
     }
     const R Dslope = D * slope;
     est[0] = D * pay;
-    est[1] = Dslope * A / S0;
-    est[2] = Dslope * A / (S0 * S0) * (lr - R(1));
+    est[1] = Dslope * A * cs.inv_S0;
+    est[2] = Dslope * A * cs.inv_S0sq * (lr - R(1));
     est[3] = Dslope * dAv;
-    est[4] = (cs.payoff[c] == HESTON_EUROPEAN) ? Dslope * K * T : Dslope * dAr - T * est[0];
-    est[5] = r * est[0] - Dslope * dAT;
+    est[4] = euro ? Dslope * K * T : Dslope * dAr - T * est[0];
+    est[5] = cs.r * est[0] - Dslope * dAT;
 }
 
 template <typename R>
@@ -315,7 +338,7 @@ enum { MON_NONE = 0, MON_EVERY = 1, MON_STRIDE = 2 };
 template <typename R, int TRUNC, int MON, int NP>
 __device__ __forceinline__ void simulate(PathState<R> (&s)[NP], const uint32_t (&plo)[NP],
                                          const uint32_t (&phi)[NP], const Coef<R> &k,
-                                         const ContractSet &cs, PhiloxKey key, uint32_t N)
+                                         const ContractSet<R> &cs, PhiloxKey key, uint32_t N)
 {
 #pragma unroll
     for (int q = 0; q < NP; ++q) init_state(s[q], k.v0);
@@ -339,11 +362,11 @@ __device__ __forceinline__ void simulate(PathState<R> (&s)[NP], const uint32_t (
             if (MON == MON_EVERY) {
                 const bool first = (h == 0) && (j == 0);
 #pragma unroll
-                for (int q = 0; q < NP; ++q) monitor(s[q], R(kp1), first);
+                for (int q = 0; q < NP; ++q) monitor(s[q], first);
             } else if (MON == MON_STRIDE) {
                 if (kp1 == next_mon) {
 #pragma unroll
-                    for (int q = 0; q < NP; ++q) monitor(s[q], R(kp1), kp1 == stride);
+                    for (int q = 0; q < NP; ++q) monitor(s[q], kp1 == stride);
                     next_mon += stride;
                 }
             }
@@ -359,7 +382,7 @@ __device__ __forceinline__ void simulate(PathState<R> (&s)[NP], const uint32_t (
         }
         if (MON == MON_EVERY || (MON == MON_STRIDE && N == next_mon)) {
 #pragma unroll
-            for (int q = 0; q < NP; ++q) monitor(s[q], R(N), N == stride);
+            for (int q = 0; q < NP; ++q) monitor(s[q], N == stride);
         }
     }
 }
@@ -371,12 +394,13 @@ __device__ __forceinline__ void simulate(PathState<R> (&s)[NP], const uint32_t (
 // butterfly), so tile rows do not depend on the launch shape.
 // ---------------------------------------------------------------------------
 template <typename R, int TRUNC, int MON>
-__global__ void __launch_bounds__(kPathBlock) heston_paths_kernel(Coef<R> k, ContractSet cs, Launch a)
+__global__ void __launch_bounds__(kPathBlock) heston_paths_kernel(Coef<R> k, ContractSet<R> cs, Launch a)
 {
     const int lane = threadIdx.x & 31;
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    const int width = 12 * cs.n;
+    const int nc = cs.n;
+    const int width = 12 * nc;
 
     for (uint64_t tile = warp; tile < a.n_tiles; tile += n_warps) {
         PathState<R> s[2];
@@ -396,17 +420,19 @@ __global__ void __launch_bounds__(kPathBlock) heston_paths_kernel(Coef<R> k, Con
 #pragma unroll
         for (int q = 0; q < 2; ++q) eT[q] = exp_r(s[q].X);
         double *row = a.tile_sums + tile * (uint64_t)width;
-        for (int c = 0; c < cs.n; ++c) {
+#pragma unroll
+        for (int c = 0; c < kMaxC; ++c) {
+            if (c >= nc) break;
             R e0[6], e1[6];
-            estimators(s[0], cs, c, eT[0], k.dt, e0);
-            estimators(s[1], cs, c, eT[1], k.dt, e1);
+            estimators(s[0], cs, c, eT[0], e0);
+            estimators(s[1], cs, c, eT[1], e1);
 #pragma unroll
             for (int j = 0; j < 6; ++j) {
                 const R x0 = keep[0] ? e0[j] : R(0), x1 = keep[1] ? e1[j] : R(0);
                 const R sx = warp_sum(x0 + x1);
                 const R sxx = warp_sum(x0 * x0 + x1 * x1);
                 if (lane == j) row[c * 6 + j] = (double)sx;
-                if (lane == 6 + j) row[6 * cs.n + c * 6 + j] = (double)sxx;
+                if (lane == 6 + j) row[6 * nc + c * 6 + j] = (double)sxx;
             }
         }
     }
@@ -415,7 +441,7 @@ __global__ void __launch_bounds__(kPathBlock) heston_paths_kernel(Coef<R> k, Con
 // Test kernel: one thread per requested path, the same step code, writes the
 // per-path record and estimators.
 template <typename R, int TRUNC, int MON>
-__global__ void heston_debug_kernel(Coef<R> k, ContractSet cs, PhiloxKey key, uint32_t N,
+__global__ void heston_debug_kernel(Coef<R> k, ContractSet<R> cs, PhiloxKey key, uint32_t N,
                                     const uint64_t *paths, uint32_t count, double *rec, double *est)
 {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -425,13 +451,13 @@ __global__ void heston_debug_kernel(Coef<R> k, ContractSet cs, PhiloxKey key, ui
     const uint32_t plo[1] = {(uint32_t)g}, phi[1] = {(uint32_t)(g >> 32)};
     simulate<R, TRUNC, MON, 1>(s, plo, phi, k, cs, key, N);
     const R eT = exp_r(s[0].X);
-    const double S0 = cs.S0;
+    const double S0 = (double)cs.S0, M = (double)cs.M;
     double *o = rec + (uint64_t)i * kRecordDoubles;
     o[0] = (double)s[0].X;   o[1] = (double)s[0].V;
     o[2] = (double)s[0].Xv;  o[3] = (double)s[0].Vv;
     o[4] = (double)s[0].XT;  o[5] = (double)s[0].VT;
     o[6] = S0 * (double)s[0].sA;
-    o[7] = S0 * (double)k.dt * (double)s[0].sB;
+    o[7] = S0 * ((double)cs.T / M) * ((M + 1.0) * (double)s[0].sA - (double)s[0].sC);
     o[8] = S0 * (double)s[0].sAv;
     o[9] = S0 * (double)s[0].sAT;
     o[10] = (double)s[0].GE; o[11] = (double)s[0].QE;
@@ -439,7 +465,7 @@ __global__ void heston_debug_kernel(Coef<R> k, ContractSet cs, PhiloxKey key, ui
     o[14] = 0.0;
     for (int c = 0; c < cs.n; ++c) {
         R e[6];
-        estimators(s[0], cs, c, eT, k.dt, e);
+        estimators(s[0], cs, c, eT, e);
         for (int j = 0; j < 6; ++j) est[((uint64_t)i * cs.n + c) * 6 + j] = (double)e[j];
     }
 }
@@ -527,13 +553,18 @@ struct DeviceGuard {
 };
 
 struct Prepared {
-    ContractSet cs;
+    ContractSet<double> cs;
+    ContractSet<float> csf;
     Coef<float> kf;
     Coef<double> kd;
     heston_options opt;
     uint32_t N;
     bool gamma_nan;
 };
+
+template <typename R> const ContractSet<R> &cs_of(const Prepared &pp);
+template <> const ContractSet<double> &cs_of<double>(const Prepared &pp) { return pp.cs; }
+template <> const ContractSet<float> &cs_of<float>(const Prepared &pp) { return pp.csf; }
 
 bool finite_nonneg(double x) { return std::isfinite(x) && x >= 0.0; }
 
@@ -566,7 +597,7 @@ int validate_and_prepare(const heston_params *p, const heston_contract *c, uint3
 
     const double T = c[0].T;
     if (!(std::isfinite(T) && T > 0.0)) return HESTON_ERR_INVALID_ARG;
-    ContractSet cs;
+    ContractSet<double> cs;
     std::memset(&cs, 0, sizeof(cs));
     cs.n = (int32_t)nc;
     uint32_t M = 0;
@@ -591,9 +622,27 @@ int validate_and_prepare(const heston_params *p, const heston_contract *c, uint3
     cs.stride = N / M;
     cs.T = T;
     cs.D = std::exp(-p->r * T);
-    cs.S0 = p->S0;
     cs.r = p->r;
-    cs.sq = std::sqrt(1.0 - p->rho * p->rho);
+    cs.S0 = p->S0;
+    cs.inv_S0 = 1.0 / p->S0;
+    cs.inv_S0sq = 1.0 / (p->S0 * p->S0);
+    const double sq = std::sqrt(1.0 - p->rho * p->rho);
+    cs.inv_sq = 1.0 / sq;           // inf at |rho| = 1: Gamma is then reported as NaN
+    cs.S0_over_M = p->S0 / (double)M;
+    cs.dAr_scale = p->S0 * T / ((double)M * (double)M);
+    cs.Mp1 = (double)M + 1.0;
+    ContractSet<float> csf;
+    std::memset(&csf, 0, sizeof(csf));
+    csf.n = cs.n; csf.has_asian = cs.has_asian; csf.M = cs.M; csf.stride = cs.stride;
+    for (int i = 0; i < kMaxC; ++i) {
+        csf.payoff[i] = cs.payoff[i];
+        csf.is_put[i] = cs.is_put[i];
+        csf.K[i] = (float)cs.K[i];
+    }
+    csf.T = (float)cs.T; csf.D = (float)cs.D; csf.r = (float)cs.r;
+    csf.S0 = (float)cs.S0; csf.inv_S0 = (float)cs.inv_S0; csf.inv_S0sq = (float)cs.inv_S0sq;
+    csf.inv_sq = (float)cs.inv_sq; csf.S0_over_M = (float)cs.S0_over_M;
+    csf.dAr_scale = (float)cs.dAr_scale; csf.Mp1 = (float)cs.Mp1;
 
     const double dt = T / (double)N;
     const double ddt = 1.0 / (double)N;
@@ -611,7 +660,7 @@ int validate_and_prepare(const heston_params *p, const heston_contract *c, uint3
     kd.c4 = 0.25 * p->xi * p->xi * dt;
     kd.c4T = 0.25 * p->xi * p->xi * ddt;
     kd.rho = p->rho;
-    kd.sq = cs.sq;
+    kd.sq = sq;
     Coef<float> kf;
     kf.v0 = (float)kd.v0; kf.dt = (float)kd.dt; kf.ddt = (float)kd.ddt;
     kf.half_dt = (float)kd.half_dt; kf.r = (float)kd.r; kf.kdt = (float)kd.kdt;
@@ -620,6 +669,7 @@ int validate_and_prepare(const heston_params *p, const heston_contract *c, uint3
     kf.rho = (float)kd.rho; kf.sq = (float)kd.sq;
 
     out.cs = cs;
+    out.csf = csf;
     out.kd = kd;
     out.kf = kf;
     out.opt = o;
@@ -664,11 +714,11 @@ cudaError_t launch_paths_t(const Prepared &pp, const Coef<R> &k, const Launch &a
         grid = need < full ? need : full;
     }
     if (grid < 1) grid = 1;
-    kern<<<(unsigned)grid, block, 0, st>>>(k, pp.cs, a);
+    kern<<<(unsigned)grid, block, 0, st>>>(k, cs_of<R>(pp), a);
     return cudaGetLastError();
 }
 
-int mon_mode(const ContractSet &cs)
+int mon_mode(const ContractSet<double> &cs)
 {
     if (!cs.has_asian) return MON_NONE;
     return cs.stride == 1 ? MON_EVERY : MON_STRIDE;
@@ -907,7 +957,7 @@ int heston_mc_debug_paths(const heston_params *params, const heston_contract *co
         const PhiloxKey key = key_of(rng_seed);
         const int mon = mon_mode(pp.cs);
         const bool full = pp.opt.trunc == HESTON_TRUNC_FULL;
-#define HESTON_DBG(R, TR, MO, K) heston_debug_kernel<R, TR, MO><<<grid, 128, 0, st>>>(K, pp.cs, key, pp.N, dp, count, dr, de)
+#define HESTON_DBG(R, TR, MO, K) heston_debug_kernel<R, TR, MO><<<grid, 128, 0, st>>>(K, cs_of<R>(pp), key, pp.N, dp, count, dr, de)
 #define HESTON_DBG_M(R, TR, K) do { if (mon == MON_NONE) HESTON_DBG(R, TR, MON_NONE, K); \
                                     else if (mon == MON_EVERY) HESTON_DBG(R, TR, MON_EVERY, K); \
                                     else HESTON_DBG(R, TR, MON_STRIDE, K); } while (0)

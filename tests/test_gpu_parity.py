@@ -3,8 +3,10 @@
 Tolerances:
   * random-number contract: Philox words bit-exact; FP64 normals within
     1e-14; FP32 normals within 1e-7 + 1.5e-6 R (R = sqrt(Za^2 + Zb^2)): the
-    documented bounds of sqrt.approx / rsqrt (2^-22 relative), logf (1 ulp)
-    and sin/cos.approx (2^-20.9 absolute on [-pi, pi]) give about 9e-7 R.
+    documented bounds of sqrt.approx (2^-22 relative), lg2.approx (2^-22
+    absolute, used only where R >= 0.46, giving |dR| <= 3.6e-7) or the
+    near-1 series (1.4e-8 relative), and sin/cos.approx (2^-20.9 absolute on
+    [-pi, pi]) give about 9e-7 R + 3.6e-7 at the switch.
   * per path, FP64 path: every record field and estimator within 1e-9
     relative (libm rounding only).
   * per path, FP32 path: X_N, V_N and the payoff underlyings within 1e-5
