@@ -21,7 +21,8 @@
  *     negative HESTON_ERR_* code; on error nothing is launched and no output
  *     is written unless stated.  No C++ exception crosses this interface.
  *   - Calls on different streams may run concurrently from different host
- *     threads; the library holds no global mutable state.
+ *     threads; the library holds no global mutable state apart from the
+ *     static scratch array of heston_mc_launch_noalloc.
  *
  * Random numbers (the contract both the GPU path and the test oracle
  * implement): Philox4x32-10 (Salmon et al., SC'11) with key = rng_seed
@@ -155,6 +156,44 @@ int heston_mc_launch(const heston_params *params, const heston_contract *contrac
                      uint32_t n_contracts, uint64_t n_paths, uint32_t n_steps,
                      uint64_t rng_seed, const heston_options *opts,
                      void *d_workspace, size_t workspace_bytes, double *d_out);
+
+/* ---- allocation-free launch ---------------------------------------------- */
+
+/* The paper has no counterpart to this entry point.  It exists for callers
+ * that must not allocate device memory themselves or let a library do it:
+ * a pricing engine embedded in a host application whose device memory is
+ * owned by another allocator (a framework's caching allocator or a fixed
+ * arena that a third-party cudaMalloc would fragment or overrun), and
+ * latency-critical request loops, where cudaMalloc / cudaFree can
+ * synchronise the device and stall work on other streams.
+ *
+ * HESTON_NOALLOC_SCRATCH_BYTES is the size of the library's static device
+ * scratch array (16 MiB); every GPU that loads the library holds it until
+ * the process exits.  A request fits when heston_mc_workspace_bytes() for
+ * its (n_contracts, n_paths) is at most this size: e.g. up to about 1.8 M
+ * paths for 6 contracts, or 11 M paths for 1 contract. */
+#define HESTON_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* Same estimate, inputs and output as heston_mc_launch, with the workspace
+ * taken from the static scratch array instead of the caller: enqueues on
+ * opts->cuda_stream and returns at once; d_out: device array of
+ * n_contracts x 12 doubles (layout as for heston_mc_launch).
+ *   - Calls no cudaMalloc, cudaFree or other allocating routine.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture on the device.
+ *   - A request larger than HESTON_NOALLOC_SCRATCH_BYTES returns
+ *     HESTON_ERR_WORKSPACE and launches nothing; other errors as for
+ *     heston_mc_launch (HESTON_ERR_INVALID_ARG also for d_out == NULL).
+ *   - All calls on a device share the one array, which keeps the last
+ *     call's contents.  Every call writes the rows it reads before reading
+ *     them, so nothing needs clearing; but calls whose kernels overlap on
+ *     the GPU (different streams or host threads without ordering between
+ *     them) race on the array and give wrong results: order them, e.g. on
+ *     one stream. */
+int heston_mc_launch_noalloc(const heston_params *params, const heston_contract *contracts,
+                             uint32_t n_contracts, uint64_t n_paths, uint32_t n_steps,
+                             uint64_t rng_seed, const heston_options *opts, double *d_out);
 
 /* ---- sharding: path-range partial sums and their reduction -------------- */
 

@@ -25,6 +25,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 
 #include "heston_mc.h"
 
@@ -795,6 +796,35 @@ void fill_results(const double *h, uint32_t nc, uint64_t n_paths, int status, he
 
 }  // namespace
 
+// Static device scratch of heston_mc_launch_noalloc (see include/heston_mc.h):
+// one array per device that loads the library, shared by every call on it.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[HESTON_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[kNoallocMaxDevices];   // device address of g_noalloc_scratch, per device
+
+// Device address of the scratch array on the current device, looked up once.
+int noalloc_scratch(void **out)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return HESTON_ERR_CUDA;
+    if (dev < 0 || dev >= kNoallocMaxDevices) return HESTON_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return HESTON_ERR_CUDA;
+        }
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return HESTON_OK;
+}
+}  // namespace
+
 // ===========================================================================
 // C ABI
 // ===========================================================================
@@ -836,6 +866,27 @@ int heston_mc_launch(const heston_params *params, const heston_contract *contrac
     DeviceGuard g(pp.opt.device);
     if (g.err != cudaSuccess) return HESTON_ERR_CUDA;
     const int e = enqueue(pp, n_paths, rng_seed, d_workspace, workspace_bytes_, d_out,
+                          (cudaStream_t)pp.opt.cuda_stream);
+    if (e < 0) return e;
+    return pp.gamma_nan ? HESTON_WARN_GAMMA_UNDEFINED : HESTON_OK;
+}
+
+int heston_mc_launch_noalloc(const heston_params *params, const heston_contract *contracts,
+                             uint32_t n_contracts, uint64_t n_paths, uint32_t n_steps,
+                             uint64_t rng_seed, const heston_options *opts, double *d_out)
+{
+    Prepared pp;
+    int rc = validate_and_prepare(params, contracts, n_contracts, n_paths, n_steps, opts, pp);
+    if (rc < 0) return rc;
+    if (!d_out) return HESTON_ERR_INVALID_ARG;
+    if (workspace_bytes(n_contracts, n_paths) > (size_t)HESTON_NOALLOC_SCRATCH_BYTES)
+        return HESTON_ERR_WORKSPACE;
+    DeviceGuard g(pp.opt.device);
+    if (g.err != cudaSuccess) return HESTON_ERR_CUDA;
+    void *scratch = nullptr;
+    rc = noalloc_scratch(&scratch);
+    if (rc < 0) return rc;
+    const int e = enqueue(pp, n_paths, rng_seed, scratch, HESTON_NOALLOC_SCRATCH_BYTES, d_out,
                           (cudaStream_t)pp.opt.cuda_stream);
     if (e < 0) return e;
     return pp.gamma_nan ? HESTON_WARN_GAMMA_UNDEFINED : HESTON_OK;

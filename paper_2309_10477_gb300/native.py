@@ -27,6 +27,7 @@ HESTON_ERR_UNSUPPORTED = -6
 HESTON_ERR_WORKSPACE = -7
 HESTON_MAX_CONTRACTS = 8
 HESTON_TILE_PATHS = 64
+HESTON_NOALLOC_SCRATCH_BYTES = 16 << 20
 
 HESTON_EUROPEAN, HESTON_ASIAN_ARITH = 0, 1
 HESTON_TRUNC_FULL, HESTON_TRUNC_PAPER_FLOOR = 0, 1
@@ -90,6 +91,8 @@ def load():
         "heston_mc_workspace_bytes": ([u32, u64, P(sz)], i32),
         "heston_mc_launch": ([P(heston_params), P(heston_contract), u32, u64, u32, u64,
                               P(heston_options), vp, sz, vp], i32),
+        "heston_mc_launch_noalloc": ([P(heston_params), P(heston_contract), u32, u64, u32, u64,
+                                      P(heston_options), vp], i32),
         "heston_mc_launch_tiles": ([P(heston_params), P(heston_contract), u32, u64, u64, u32, u64,
                                     P(heston_options), vp], i32),
         "heston_mc_reduce_tiles": ([vp, u64, u32, u64, vp, sz, vp, vp], i32),
@@ -181,6 +184,16 @@ def heston_mc_launch(params, contracts, n_paths, n_steps, rng_seed, options, wor
     return _check(load().heston_mc_launch(ctypes.byref(params), cs, len(contracts), n_paths,
                                           n_steps, rng_seed, ctypes.byref(options), _ptr(workspace),
                                           workspace_bytes, _ptr(out)))
+
+
+def heston_mc_launch_noalloc(params, contracts, n_paths, n_steps, rng_seed, options, out) -> int:
+    """heston_mc_launch with the library's static device scratch: for callers
+    that must not allocate device memory (see include/heston_mc.h).  ``out``
+    is a device buffer of 12 doubles per contract."""
+    cs = _contract_array(contracts)
+    return _check(load().heston_mc_launch_noalloc(ctypes.byref(params), cs, len(contracts),
+                                                  n_paths, n_steps, rng_seed,
+                                                  ctypes.byref(options), _ptr(out)))
 
 
 def heston_mc_launch_tiles(params, contracts, path_begin, n_paths, n_steps, rng_seed, options,
