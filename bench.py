@@ -285,6 +285,42 @@ def run_gpu(args):
     ms, k1 = float(t[0]), float(t[1])
     estimates = out.view(nc, 12).cpu().numpy()
 
+    # randomised-QMC variant on the same workload: 32 replicates x 2^17 points
+    qmc = None
+    if not args.no_qmc and world == 1:
+        R = 32
+        tb_bytes = nv.heston_qmc_tables_bytes(w.n_steps)
+        tables = torch.empty(tb_bytes // 8 + 1, dtype=torch.float64, device=dev)
+        nv.heston_qmc_build_tables(w.n_steps, tables, tb_bytes, local)
+        qws_bytes = nv.heston_mc_workspace_bytes_qmc(nc, n, w.n_steps, R)
+        qws = torch.empty(qws_bytes // 8 + 1, dtype=torch.float64, device=dev)
+        qout = torch.empty(nc * 12, dtype=torch.float64, device=dev)
+        qopts = nv.make_options(prec=nv.HESTON_FP32, stream=stream, device=local,
+                                rng=nv.HESTON_RNG_SOBOL_BB, n_shifts=R)
+        for _ in range(3):
+            nv.heston_mc_launch_qmc(params, contracts, n, w.n_steps, w.seed, qopts, tables, qws,
+                                    qws_bytes, qout)
+        barrier()
+        q_steps = max(3, min(args.steps, 50))
+        qev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(q_steps)]
+        clocks.mark(True)
+        for i in range(q_steps):
+            flush.fill_(i & 0xFF)
+            qev[i][0].record(stream)
+            nv.heston_mc_launch_qmc(params, contracts, n, w.n_steps, w.seed, qopts, tables, qws,
+                                    qws_bytes, qout)
+            qev[i][1].record(stream)
+        barrier()
+        clocks.mark(False)
+        q_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in qev)
+        qest = qout.view(nc, 12).cpu().numpy()
+        se_ratio = float(qest[1, 6] / estimates[1, 6])          # price SE, European K=100
+        qmc = {"rng": "sobol+brownian-bridge, 32 digital shifts x 2^17 points",
+               "ms_per_step": q_ms, "path_steps_per_s": n * w.n_steps / (q_ms * 1e-3),
+               "price_se_k100_euro": float(qest[1, 6]), "se_ratio_vs_philox": se_ratio,
+               "path_steps_per_s_at_philox_se": n * w.n_steps / (q_ms * 1e-3) / se_ratio**2,
+               "gpu_launches_per_step": 4}
+
     # end to end through the synchronous host API (host structs in, results out)
     res_arr = (nv.heston_result * nc)()
     carr = (nv.heston_contract * nc)(*contracts)
@@ -347,6 +383,8 @@ def run_gpu(args):
                          "path_steps_per_s_kernel": path_steps / (k1 * 1e-3)},
             "clocks": clk,
         }
+        if qmc is not None:
+            line["qmc_variant"] = qmc
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
         print(json.dumps(line), flush=True)
@@ -363,6 +401,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-qmc", action="store_true", help="skip the quasi-Monte Carlo variant")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--n-paths", type=int, default=0,
                     help="paths per rank (default: the workload's 2^22); small cases for ncu")

@@ -92,7 +92,8 @@ typedef enum { HESTON_FP32 = 0, HESTON_FP64 = 1 } heston_prec;
  * cuda_stream: a cudaStream_t (NULL = legacy default stream).  device:
  * CUDA ordinal, or -1 for the calling thread's current device.
  * grid_ctas / block_threads: launch shape of the path kernel (0 = choose);
- * results do not depend on them.  n_shifts: reserved for the QMC variant. */
+ * results do not depend on them.  rng: Philox (pseudo-random) or the
+ * randomised-QMC variant below, with n_shifts replicates. */
 typedef struct {
     int32_t trunc;
     int32_t rng;
@@ -217,6 +218,72 @@ int heston_mc_launch_tiles(const heston_params *params, const heston_contract *c
 int heston_mc_reduce_tiles(const double *d_tile_sums, uint64_t n_tiles, uint32_t n_contracts,
                            uint64_t n_paths_total, void *d_workspace, size_t workspace_bytes,
                            double *d_out, void *stream);
+
+/* ---- randomised quasi-Monte Carlo variant ------------------------------- */
+
+/* Normals from a Sobol sequence randomised by digital shifts and fed
+ * through a Brownian bridge (Sobol sequences and Property A: Sec. 2.7; the
+ * paper found plain QMC unsatisfactory for the discretised schemes, Sec. 3,
+ * which the bridge addresses by putting the coarse shape of each Brownian
+ * motion in the first dimensions).  Definitions shared with the test oracle:
+ *   - 2 n_steps dimensions; dimension 0: v_k = 2^(32-k); dimension j >= 1:
+ *     the j-th primitive polynomial over GF(2) by (degree, coefficient
+ *     bits), initial numbers m_1..m_s from Philox4x32-10 with key
+ *     (0x50B01, 0) and counter ((k-1)/4, j, c, 3), word (k-1)%4,
+ *     m_k = 2 (w mod 2^(k-1)) + 1; for j < 32 the first candidate c that
+ *     keeps the leading (j+1)x(j+1) matrix of first binary digits
+ *     non-singular (Property A for the first j+1 dimensions), else c = 0;
+ *     Bratley-Fox recurrence to 32-bit direction integers.
+ *   - replicate r (of opts->n_shifts) XORs word d%4 of Philox block
+ *     (d/4, r, 0, 2) under key rng_seed into dimension d; path index
+ *     p = r * P + n with P = n_paths / n_shifts points per replicate.
+ *   - u = ((y >> 8) + 1/2) 2^-24, z = Phi^-1(u).
+ *   - Brownian bridge on the step grid 0..N: node 0 is time N; then
+ *     intervals [l, r] with r - l >= 2 are bisected breadth-first at
+ *     m = l + (r-l)/2.  Node j drives motion a (Za) with dimension 2j and
+ *     motion b (Zb) with 2j+1; step normals are the bridge increments.
+ *   - Estimates: mean over replicates of each replicate's average;
+ *     SE = sample stdev of the replicate averages / sqrt(n_shifts).
+ * Constraints: FP32 path only (HESTON_ERR_UNSUPPORTED otherwise);
+ * n_steps <= 2048; n_shifts >= 2; P a multiple of 64 and <= 2^32.
+ * heston_mc_price_greeks_ex runs this variant when opts->rng is
+ * HESTON_RNG_SOBOL_BB; the other launch entry points accept only Philox. */
+
+/* Host-built direction integers (test support): h_out, n_dims x 32 uint32,
+ * row d holds v_{d,1..32}.  n_dims <= 4096. */
+int heston_sobol_directions(uint32_t n_dims, uint32_t *h_out);
+
+/* Bytes of the device table buffer for n_steps (direction integers, the
+ * 64-point tile table and the bridge event plan). */
+int heston_qmc_tables_bytes(uint32_t n_steps, size_t *bytes);
+
+/* Build the tables for n_steps into d_tables (device, 256-byte aligned,
+ * >= heston_qmc_tables_bytes).  Synchronous (host computation and a copy);
+ * the buffer is then read-only and may serve any number of launches with
+ * the same n_steps.  device: CUDA ordinal or -1 for the current device. */
+int heston_qmc_build_tables(uint32_t n_steps, void *d_tables, size_t bytes, int32_t device);
+
+/* Workspace bytes of heston_mc_launch_qmc. */
+int heston_mc_workspace_bytes_qmc(uint32_t n_contracts, uint64_t n_paths, uint32_t n_steps,
+                                  uint32_t n_shifts, size_t *bytes);
+
+/* Enqueue a randomised-QMC estimate (opts->rng == HESTON_RNG_SOBOL_BB,
+ * opts->n_shifts replicates) on opts->cuda_stream: no allocation, no
+ * synchronisation.  d_tables: built by heston_qmc_build_tables for the same
+ * n_steps.  d_workspace: device, 256-byte aligned, >=
+ * heston_mc_workspace_bytes_qmc.  d_out: as for heston_mc_launch. */
+int heston_mc_launch_qmc(const heston_params *params, const heston_contract *contracts,
+                         uint32_t n_contracts, uint64_t n_paths, uint32_t n_steps,
+                         uint64_t rng_seed, const heston_options *opts, const void *d_tables,
+                         void *d_workspace, size_t workspace_bytes, double *d_out);
+
+/* Per-path dump of the QMC variant (test support): `count` points (host
+ * array, indices within replicate `replicate` < 2^16); records and
+ * estimators as for heston_mc_debug_paths.  Synchronous; allocates. */
+int heston_qmc_debug_paths(const heston_params *params, const heston_contract *contracts,
+                           uint32_t n_contracts, uint32_t n_steps, uint64_t rng_seed,
+                           const heston_options *opts, uint32_t replicate, const uint32_t *points,
+                           uint32_t count, double *h_records, double *h_estimators);
 
 /* ---- test support --------------------------------------------------------- */
 

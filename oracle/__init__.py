@@ -10,6 +10,8 @@ Contents:
     per-path estimators and the Monte Carlo driver of Sec. 2.5 (plain C, FP64).
   * ``closed_form`` -- Black-Scholes and the Heston characteristic-function
     price and Greeks (the "real price" the paper quotes in Sec. 3).
+  * ``sobol`` -- Sobol points, digital shifts, inverse normal and Brownian
+    bridge for the randomised quasi-Monte Carlo variant (Sec. 2.7).
 
 Parity pins live in ``tests/test_oracle_*.py``; functions with no pin say
 "parity unpinned" in their docstring.
@@ -83,6 +85,9 @@ def _load():
         lib.orc_path_from_normals.argtypes = [P(_Params), P(_Contract), u32, u32, i32, P(d), P(d),
                                               P(d), P(d), P(d), P(d)]
         lib.orc_path_from_normals.restype = i32
+        lib.orc_paths_from_normals.argtypes = [P(_Params), P(_Contract), u32, u32, i32, u64,
+                                               P(d), P(d), P(d), P(d)]
+        lib.orc_paths_from_normals.restype = i32
         lib.orc_max_threads.restype = i32
         _lib = lib
     return _lib
@@ -220,6 +225,22 @@ def path_from_normals(params: Params, contracts, za, zb, trunc=TRUNC_FULL):
                                    _dptr(zb), _dptr(rec), _dptr(est), _dptr(tx), _dptr(tv))
     _check_rc(rc)
     return rec, est, tx, tv
+
+
+def paths_from_normals(params: Params, contracts, za, zb, trunc=TRUNC_FULL):
+    """Many paths from given normals (n_paths, N): records (n, 15) and estimators (n, C, 6)."""
+    lib = _load()
+    za = np.ascontiguousarray(za, dtype=np.float64)
+    zb = np.ascontiguousarray(zb, dtype=np.float64)
+    n, N = za.shape
+    cs = _contracts(contracts)
+    rec = np.zeros((n, len(PATH_FIELDS)))
+    est = np.zeros((n, len(contracts), 6))
+    p = params._c()
+    rc = lib.orc_paths_from_normals(ctypes.byref(p), cs, len(contracts), N, trunc, n, _dptr(za),
+                                    _dptr(zb), _dptr(rec), _dptr(est))
+    _check_rc(rc)
+    return rec, est
 
 
 def max_threads() -> int:

@@ -447,6 +447,33 @@ int orc_path_from_normals(const orc_params *p, const orc_contract *contracts, ui
     return 0;
 }
 
+/* Many paths from caller-supplied normals: Za, Zb are (n_paths x N) row-major;
+ * rec receives n_paths x ORC_PATH_DOUBLES and est n_paths x n_contracts x 6. */
+int orc_paths_from_normals(const orc_params *p, const orc_contract *contracts, uint32_t n_contracts,
+                           uint32_t N, int trunc, uint64_t n_paths, const double *Za,
+                           const double *Zb, double *rec, double *est)
+{
+    if (n_contracts == 0 || N == 0) return -1;
+    uint32_t M = N;
+    for (uint32_t c = 0; c < n_contracts; ++c) {
+        if (contracts[c].T != contracts[0].T) return -1;
+        if (contracts[c].payoff == 1 && contracts[c].n_monitor) M = contracts[c].n_monitor;
+    }
+    if (N % M != 0) return -1;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+    for (int64_t i = 0; i < (int64_t)n_paths; ++i) {
+        orc_path w;
+        orc_milstein_path(p, contracts[0].T, N, M, trunc, Za + (size_t)i * N, Zb + (size_t)i * N,
+                          &w, NULL, NULL);
+        memcpy(rec + (size_t)i * ORC_PATH_DOUBLES, &w, sizeof(double) * ORC_PATH_DOUBLES);
+        for (uint32_t c = 0; c < n_contracts; ++c)
+            orc_estimators(p, &contracts[c], N, &w, est + ((size_t)i * n_contracts + c) * 6);
+    }
+    return 0;
+}
+
 int orc_max_threads(void)
 {
 #ifdef _OPENMP

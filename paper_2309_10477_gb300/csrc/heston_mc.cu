@@ -24,8 +24,12 @@
 
 #include <cmath>
 #include <cstdint>
+#include <algorithm>
 #include <cstring>
+#include <deque>
+#include <map>
 #include <mutex>
+#include <vector>
 
 #include "heston_mc.h"
 
@@ -46,7 +50,7 @@ struct PhiloxKey {
     uint32_t k0, k1;
 };
 
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, PhiloxKey key)
+__host__ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, PhiloxKey key)
 {
     uint32_t k0 = key.k0, k1 = key.k1;
 #pragma unroll
@@ -439,6 +443,30 @@ __global__ void __launch_bounds__(kPathBlock) heston_paths_kernel(Coef<R> k, Con
     }
 }
 
+// Per-path record (see heston_mc_debug_paths) and estimators of one path.
+template <typename R>
+__device__ void write_debug_record(const PathState<R> &s, const ContractSet<R> &cs, double *o,
+                                   double *est)
+{
+    const R eT = exp_r(s.X);
+    const double S0 = (double)cs.S0, M = (double)cs.M;
+    o[0] = (double)s.X;   o[1] = (double)s.V;
+    o[2] = (double)s.Xv;  o[3] = (double)s.Vv;
+    o[4] = (double)s.XT;  o[5] = (double)s.VT;
+    o[6] = S0 * (double)s.sA;
+    o[7] = S0 * ((double)cs.T / M) * ((M + 1.0) * (double)s.sA - (double)s.sC);
+    o[8] = S0 * (double)s.sAv;
+    o[9] = S0 * (double)s.sAT;
+    o[10] = (double)s.GE; o[11] = (double)s.QE;
+    o[12] = (double)s.GA; o[13] = (double)s.QA;
+    o[14] = 0.0;
+    for (int c = 0; c < cs.n; ++c) {
+        R e[6];
+        estimators(s, cs, c, eT, e);
+        for (int j = 0; j < 6; ++j) est[c * 6 + j] = (double)e[j];
+    }
+}
+
 // Test kernel: one thread per requested path, the same step code, writes the
 // per-path record and estimators.
 template <typename R, int TRUNC, int MON>
@@ -451,24 +479,7 @@ __global__ void heston_debug_kernel(Coef<R> k, ContractSet<R> cs, PhiloxKey key,
     PathState<R> s[1];
     const uint32_t plo[1] = {(uint32_t)g}, phi[1] = {(uint32_t)(g >> 32)};
     simulate<R, TRUNC, MON, 1>(s, plo, phi, k, cs, key, N);
-    const R eT = exp_r(s[0].X);
-    const double S0 = (double)cs.S0, M = (double)cs.M;
-    double *o = rec + (uint64_t)i * kRecordDoubles;
-    o[0] = (double)s[0].X;   o[1] = (double)s[0].V;
-    o[2] = (double)s[0].Xv;  o[3] = (double)s[0].Vv;
-    o[4] = (double)s[0].XT;  o[5] = (double)s[0].VT;
-    o[6] = S0 * (double)s[0].sA;
-    o[7] = S0 * ((double)cs.T / M) * ((M + 1.0) * (double)s[0].sA - (double)s[0].sC);
-    o[8] = S0 * (double)s[0].sAv;
-    o[9] = S0 * (double)s[0].sAT;
-    o[10] = (double)s[0].GE; o[11] = (double)s[0].QE;
-    o[12] = (double)s[0].GA; o[13] = (double)s[0].QA;
-    o[14] = 0.0;
-    for (int c = 0; c < cs.n; ++c) {
-        R e[6];
-        estimators(s[0], cs, c, eT, e);
-        for (int j = 0; j < 6; ++j) est[((uint64_t)i * cs.n + c) * 6 + j] = (double)e[j];
-    }
+    write_debug_record(s[0], cs, rec + (uint64_t)i * kRecordDoubles, est + (uint64_t)i * cs.n * 6);
 }
 
 template <typename R>
@@ -487,6 +498,263 @@ __global__ void rng_debug_kernel(PhiloxKey key, const uint64_t *paths, const uin
     else         box_muller(w.x, w.y, za, zb);
     normals[2 * i] = (double)za;
     normals[2 * i + 1] = (double)zb;
+}
+
+
+// ---------------------------------------------------------------------------
+// Randomised quasi-Monte Carlo normals (Sec. 2.7): a Sobol sequence with
+// digital shifts, fed through a Brownian bridge so that the first dimensions
+// carry the coarse shape of both Brownian motions.  Definitions (the test
+// oracle implements the same ones separately):
+//   * dimension 0: v_k = 2^(32-k); dimension j >= 1: the j-th primitive
+//     polynomial over GF(2) ordered by (degree, coefficient bits), initial
+//     m_1..m_s from Philox (key 0x50B01, counter ((k-1)/4, j, c, 3), word
+//     (k-1)%4, m_k = 2 (w mod 2^(k-1)) + 1); for j < 32 the first candidate c
+//     that keeps the leading (j+1)x(j+1) first-digit matrix non-singular
+//     over GF(2) (Property A), else c = 0; Bratley-Fox recurrence.
+//   * replicate r's shift of dimension d: Philox (seed key) counter
+//     (d/4, r, 0, 2), word d%4; y = x_d(point) XOR shift.
+//   * u = ((y >> 8) + 1/2) 2^-24, z = Phi^-1(u).
+//   * Brownian bridge on the step grid 0..N: node 0 = time N; then
+//     breadth-first bisection m = l + (r-l)/2 of intervals with r - l >= 2.
+//     Node j drives motion a with dimension 2j and motion b with 2j+1.
+// In the kernel the bridge runs in time order: a per-thread stack holds W at
+// the right ends of the open intervals.  Entering step k (W_k known), the
+// plan pushes W_m = W_k + (m-k)/(r-k) (W_r - W_k) + sqrt((m-k)(r-m)/(r-k)) z
+// for the nodes m of [k, r] down to [k, k+1] (r: the stack top), then pops
+// W_{k+1}; the step normal is W_{k+1} - W_k.  Every W is interpolated from
+// two stored values, so FP32 rounding does not accumulate along the path.
+// ---------------------------------------------------------------------------
+constexpr int kQmcMaxLevels = 14;           // stack slots (slot 0 = 0); n_steps <= 2048
+constexpr uint32_t kQmcMaxSteps = 2048;
+constexpr uint32_t kSobolKey0 = 0x50B01u, kSobolKey1 = 0u;
+constexpr uint32_t kSobolInitTag = 3u, kSobolShiftTag = 2u;
+
+struct BridgeOp {
+    int32_t node;       // node j: normals from dimensions 2j and 2j+1
+    float a;            // (m - k) / (r - k)
+    float s;            // sqrt((m - k)(r - m) / (r - k)); node 0: a = 0, s = sqrt(N)
+    int32_t pad;
+};
+
+struct QmcTables {
+    const uint32_t *V;        // [D][32] direction integers
+    const uint32_t *T;        // [D][64] x_d(p) for the 64 points p of a tile
+    const BridgeOp *ev;       // stack pushes, step-major
+    const int32_t *ev_off;    // [N + 1] first push of each step
+};
+
+struct QmcLaunch {
+    QmcTables tb;
+    const uint32_t *U;        // [tiles per replicate][D]: x_d(64 t), high bits of the point
+    const uint32_t *shift;    // [replicates][D]
+    uint32_t D, N, tpr;       // Sobol dims (2N), steps, tiles per replicate
+    uint64_t n_tiles;
+    double *tile_sums;
+};
+
+// Phi^-1 of the 24-bit uniform of y, taking the lower half by symmetry so that
+// the FP32 uniform (2k + 1) 2^-25 is exact and never 1.
+__device__ __forceinline__ float qmc_normal(uint32_t y)
+{
+    const uint32_t k = y >> 8;
+    const bool upper = k >= 0x800000u;
+    const uint32_t kk = upper ? 0xFFFFFFu - k : k;
+    const float u = (float)(2u * kk + 1u) * 2.98023223876953125e-8f;
+    const float z = normcdfinvf(u);
+    return upper ? -z : z;
+}
+
+// NP paths of one lane through all N steps with bridge normals.  pos[q]: the
+// path's position in its 64-point tile; U / Sh: the tile's high-bit Sobol
+// integers and the replicate's shifts.
+template <int TRUNC, int MON, int NP>
+__device__ __forceinline__ void simulate_qmc(PathState<float> (&s)[NP], const uint32_t (&pos)[NP],
+                                             const Coef<float> &k, const ContractSet<float> &cs,
+                                             const QmcTables &tb, const uint32_t *U,
+                                             const uint32_t *Sh, uint32_t N)
+{
+    float st[NP][2][kQmcMaxLevels];             // W at pending right ends; slot 0 = 0
+    float Wk[NP][2];                            // W at the current time
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        init_state(s[q], k.v0);
+        Wk[q][0] = 0.0f;
+        Wk[q][1] = 0.0f;
+        st[q][0][0] = 0.0f;
+        st[q][1][0] = 0.0f;
+    }
+    int top = 0;
+    const uint32_t stride = cs.stride;
+    uint32_t next_mon = stride;
+    for (uint32_t kk = 0; kk < N; ++kk) {
+        const int e1 = tb.ev_off[kk + 1];
+        for (int e = tb.ev_off[kk]; e < e1; ++e) {
+            const BridgeOp op = tb.ev[e];
+#pragma unroll
+            for (int mu = 0; mu < 2; ++mu) {
+                const uint32_t dim = 2u * (uint32_t)op.node + (uint32_t)mu;
+                const uint32_t hi = U[dim] ^ Sh[dim];
+#pragma unroll
+                for (int q = 0; q < NP; ++q) {
+                    const float z = qmc_normal(tb.T[dim * 64u + pos[q]] ^ hi);
+                    const float Wr = st[q][mu][top];
+                    st[q][mu][top + 1] = fmaf(op.s, z, fmaf(op.a, Wr - Wk[q][mu], Wk[q][mu]));
+                }
+            }
+            ++top;
+        }
+        float za[NP], zb[NP];
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            const float wa = st[q][0][top], wb = st[q][1][top];
+            za[q] = wa - Wk[q][0];
+            zb[q] = wb - Wk[q][1];
+            Wk[q][0] = wa;
+            Wk[q][1] = wb;
+        }
+        --top;
+#pragma unroll
+        for (int q = 0; q < NP; ++q) milstein_step<float, TRUNC>(s[q], za[q], zb[q], k);
+        const uint32_t kp1 = kk + 1u;
+        if (MON == MON_EVERY) {
+#pragma unroll
+            for (int q = 0; q < NP; ++q) monitor(s[q], kk == 0);
+        } else if (MON == MON_STRIDE) {
+            if (kp1 == next_mon) {
+#pragma unroll
+                for (int q = 0; q < NP; ++q) monitor(s[q], kp1 == stride);
+                next_mon += stride;
+            }
+        }
+    }
+}
+
+// QMC path kernel: same tile layout and epilogue as heston_paths_kernel.
+// Tile t belongs to replicate t / tpr; every tile is full (points per
+// replicate are a multiple of 64).
+template <int TRUNC, int MON>
+__global__ void __launch_bounds__(kPathBlock) heston_qmc_kernel(Coef<float> k, ContractSet<float> cs,
+                                                                QmcLaunch a)
+{
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const int nc = cs.n;
+    const int width = 12 * nc;
+    for (uint64_t tile = warp; tile < a.n_tiles; tile += n_warps) {
+        const uint32_t rep = (uint32_t)(tile / a.tpr), tin = (uint32_t)(tile % a.tpr);
+        PathState<float> s[2];
+        const uint32_t pos[2] = {(uint32_t)lane, (uint32_t)lane + 32u};
+        simulate_qmc<TRUNC, MON, 2>(s, pos, k, cs, a.tb, a.U + (uint64_t)tin * a.D,
+                                    a.shift + (uint64_t)rep * a.D, a.N);
+        float eT[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) eT[q] = exp_r(s[q].X);
+        double *row = a.tile_sums + tile * (uint64_t)width;
+#pragma unroll
+        for (int c = 0; c < kMaxC; ++c) {
+            if (c >= nc) break;
+            float e0[6], e1[6];
+            estimators(s[0], cs, c, eT[0], e0);
+            estimators(s[1], cs, c, eT[1], e1);
+#pragma unroll
+            for (int j = 0; j < 6; ++j) {
+                const float sx = warp_sum(e0[j] + e1[j]);
+                const float sxx = warp_sum(e0[j] * e0[j] + e1[j] * e1[j]);
+                if (lane == j) row[c * 6 + j] = (double)sx;
+                if (lane == 6 + j) row[6 * nc + c * 6 + j] = (double)sxx;
+            }
+        }
+    }
+}
+
+// Per-launch tables: U[t][d] = x_d(64 t) and the replicates' digital shifts.
+__global__ void qmc_setup_kernel(const uint32_t *V, uint32_t D, uint32_t tpr, uint32_t R,
+                                 PhiloxKey key, uint32_t *U, uint32_t *shift)
+{
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t nU = (uint64_t)tpr * D;
+    if (i < nU) {
+        const uint32_t t = (uint32_t)(i / D), d = (uint32_t)(i % D);
+        const uint64_t n = (uint64_t)t * 64u;
+        uint32_t x = 0;
+        for (int b = 6; b < 32; ++b)
+            if ((n >> b) & 1u) x ^= V[d * 32u + b];
+        U[i] = x;
+    } else if (i < nU + (uint64_t)R * D) {
+        const uint64_t j = i - nU;
+        const uint32_t r = (uint32_t)(j / D), d = (uint32_t)(j % D);
+        const uint4 w = philox4x32_10(make_uint4(d >> 2, r, 0u, kSobolShiftTag), key);
+        const uint32_t sel = d & 3u;
+        shift[j] = sel == 0 ? w.x : sel == 1 ? w.y : sel == 2 ? w.z : w.w;
+    }
+}
+
+// Test support: Udbg[i][d] = x_d(points[i] with its low 6 bits cleared).
+__global__ void qmc_debug_high_bits_kernel(const uint32_t *V, uint32_t D, const uint32_t *points,
+                                           uint32_t count, uint32_t *Udbg)
+{
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (uint64_t)count * D) return;
+    const uint32_t p = (uint32_t)(i / D), d = (uint32_t)(i % D);
+    const uint32_t n = points[p];
+    uint32_t x = 0;
+    for (int b = 6; b < 32; ++b)
+        if ((n >> b) & 1u) x ^= V[d * 32u + b];
+    Udbg[i] = x;
+}
+
+// Test kernel: one thread per requested point of one replicate, through the
+// same simulate_qmc as the path kernel.
+template <int TRUNC, int MON>
+__global__ void heston_qmc_debug_kernel(Coef<float> k, ContractSet<float> cs, QmcTables tb,
+                                        uint32_t N, const uint32_t *points, const uint32_t *Udbg,
+                                        const uint32_t *shift_row, uint32_t count, double *rec,
+                                        double *est)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    PathState<float> s[1];
+    const uint32_t pos[1] = {points[i] & 63u};
+    simulate_qmc<TRUNC, MON, 1>(s, pos, k, cs, tb, Udbg + (uint64_t)i * 2u * N, shift_row, N);
+    write_debug_record(s[0], cs, rec + (uint64_t)i * kRecordDoubles, est + (uint64_t)i * cs.n * 6);
+}
+
+__global__ void reduce_replicates_kernel(const double *tile_sums, uint32_t tpr, int width,
+                                         double *rep_sums)
+{
+    const uint64_t r = blockIdx.x;
+    for (int col = threadIdx.x; col < width; col += blockDim.x) {
+        double acc = 0.0;
+        for (uint32_t t = 0; t < tpr; ++t) acc += tile_sums[(r * tpr + t) * (uint64_t)width + col];
+        rep_sums[r * width + col] = acc;
+    }
+}
+
+// Randomised-QMC estimate: mean over replicates of the replicate averages;
+// SE = their sample stdev / sqrt(R).
+__global__ void reduce_final_qmc_kernel(const double *rep_sums, uint32_t R, int n_contracts,
+                                        double ppr, int gamma_nan, double *out)
+{
+    const int width = 12 * n_contracts;
+    const int E = 6 * n_contracts;
+    for (int e = threadIdx.x; e < E; e += blockDim.x) {
+        double mean = 0.0;
+        for (uint32_t r = 0; r < R; ++r) mean += rep_sums[(uint64_t)r * width + e] / ppr;
+        mean /= (double)R;
+        double var = 0.0;
+        for (uint32_t r = 0; r < R; ++r) {
+            const double d = rep_sums[(uint64_t)r * width + e] / ppr - mean;
+            var += d * d;
+        }
+        var /= (double)(R - 1);
+        double se = sqrt(var / (double)R);
+        const int c = e / 6, j = e % 6;
+        if (gamma_nan && j == 2) { mean = nan(""); se = nan(""); }
+        out[c * 12 + j] = mean;
+        out[c * 12 + 6 + j] = se;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -591,7 +859,6 @@ int validate_and_prepare(const heston_params *p, const heston_contract *c, uint3
     if (o.trunc != HESTON_TRUNC_FULL && o.trunc != HESTON_TRUNC_PAPER_FLOOR) return HESTON_ERR_INVALID_ARG;
     if (o.prec != HESTON_FP32 && o.prec != HESTON_FP64) return HESTON_ERR_INVALID_ARG;
     if (o.rng != HESTON_RNG_PHILOX && o.rng != HESTON_RNG_SOBOL_BB) return HESTON_ERR_INVALID_ARG;
-    if (o.rng == HESTON_RNG_SOBOL_BB) return HESTON_ERR_UNSUPPORTED;
     if (o.reserved != 0) return HESTON_ERR_INVALID_ARG;
     if (o.block_threads != 0 && (o.block_threads % 32 != 0 || o.block_threads > kPathBlock))
         return HESTON_ERR_INVALID_ARG;
@@ -794,6 +1061,330 @@ void fill_results(const double *h, uint32_t nc, uint64_t n_paths, int status, he
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Host: QMC tables (Sobol direction integers, per-tile low-bit table, bridge
+// event plan), their layout in a caller buffer, and the QMC launch.
+// ---------------------------------------------------------------------------
+uint64_t gf2_mulmod(uint64_t a, uint64_t b, uint64_t mod, int deg)
+{
+    uint64_t r = 0;
+    while (b) {
+        if (b & 1u) r ^= a;
+        b >>= 1;
+        a <<= 1;
+        if ((a >> deg) & 1u) a ^= mod;
+    }
+    return r;
+}
+
+uint64_t gf2_powmod(uint64_t base, uint64_t e, uint64_t mod, int deg)
+{
+    uint64_t r = 1;
+    while (e) {
+        if (e & 1u) r = gf2_mulmod(r, base, mod, deg);
+        base = gf2_mulmod(base, base, mod, deg);
+        e >>= 1;
+    }
+    return r;
+}
+
+int degree_of(uint32_t poly)
+{
+    int d = -1;
+    while (poly) { ++d; poly >>= 1; }
+    return d;
+}
+
+// Primitive over GF(2): constant term 1 and x of order 2^s - 1 modulo poly.
+bool gf2_primitive(uint32_t poly)
+{
+    const int s = degree_of(poly);
+    if (s < 1 || !(poly & 1u)) return false;
+    if (s == 1) return poly == 3u;
+    const uint64_t order = (1ull << s) - 1;
+    if (gf2_powmod(2, order, poly, s) != 1) return false;
+    uint64_t n = order;
+    for (uint64_t q = 2; q * q <= n; ++q) {
+        if (n % q) continue;
+        if (gf2_powmod(2, order / q, poly, s) == 1) return false;
+        while (n % q == 0) n /= q;
+    }
+    if (n > 1 && gf2_powmod(2, order / n, poly, s) == 1) return false;
+    return true;
+}
+
+// Bratley-Fox recurrence from the initial m_1..m_s to v_1..v_32.
+void sobol_recurrence(uint32_t poly, const uint32_t *m_init, uint32_t *v)
+{
+    const int s = degree_of(poly);
+    uint64_t m[32];
+    for (int k = 0; k < s && k < 32; ++k) m[k] = m_init[k];
+    for (int k = s; k < 32; ++k) {
+        uint64_t val = m[k - s] ^ (m[k - s] << s);
+        for (int i = 1; i < s; ++i)
+            if ((poly >> (s - i)) & 1u) val ^= m[k - i] << i;
+        m[k] = val;
+    }
+    for (int k = 0; k < 32; ++k) v[k] = (uint32_t)(m[k] << (31 - k));
+}
+
+uint32_t first_digit_row(const uint32_t *v, int n_cols)
+{
+    uint32_t row = 0;
+    for (int k = 0; k < n_cols; ++k) row |= ((v[k] >> 31) & 1u) << k;
+    return row;
+}
+
+// GF(2) elimination: rows independent?
+bool gf2_independent(std::vector<uint32_t> rows)
+{
+    for (size_t i = 0; i < rows.size(); ++i) {
+        if (!rows[i]) return false;
+        const uint32_t low = rows[i] & (~rows[i] + 1u);      // pivot: lowest set bit
+        for (size_t j = i + 1; j < rows.size(); ++j)
+            if (rows[j] & low) rows[j] ^= rows[i];
+    }
+    return true;
+}
+
+void sobol_directions_host(uint32_t D, uint32_t *V)
+{
+    for (int k = 0; k < 32; ++k) V[k] = 1u << (31 - k);
+    uint32_t poly = 2;                                    // next candidate polynomial
+    const PhiloxKey key{kSobolKey0, kSobolKey1};
+    for (uint32_t j = 1; j < D; ++j) {
+        while (!gf2_primitive(poly)) ++poly;
+        const uint32_t P = poly++;
+        const int s = degree_of(P);
+        uint32_t v[32], v0[32];
+        auto candidate = [&](uint32_t c, uint32_t *out) {
+            uint32_t m[32];
+            for (int k = 1; k <= s; ++k) {
+                const uint4 w = philox4x32_10(make_uint4((uint32_t)(k - 1) / 4u, j, c, kSobolInitTag), key);
+                const int sel = (k - 1) % 4;
+                const uint32_t word = sel == 0 ? w.x : sel == 1 ? w.y : sel == 2 ? w.z : w.w;
+                m[k - 1] = 2u * (word % (1u << (k - 1))) + 1u;
+            }
+            sobol_recurrence(P, m, out);
+        };
+        candidate(0, v0);
+        const uint32_t *chosen = v0;
+        if (j < 32) {
+            const int n_cols = (int)j + 1;
+            std::vector<uint32_t> rows;
+            for (uint32_t i = 0; i < j; ++i) rows.push_back(first_digit_row(V + i * 32u, n_cols));
+            for (uint32_t c = 0; c < 64; ++c) {
+                candidate(c, v);
+                rows.push_back(first_digit_row(v, n_cols));
+                const bool ok = gf2_independent(rows);
+                rows.pop_back();
+                if (ok) { chosen = v; break; }
+            }
+        }
+        std::memcpy(V + j * 32u, chosen, sizeof(uint32_t) * 32);
+    }
+}
+
+struct BridgePlanHost {
+    uint32_t N = 0;
+    int depth = 0;
+    std::vector<BridgeOp> ev;
+    std::vector<int32_t> off;
+};
+
+// Breadth-first bisection (node indices, hence Sobol dimensions) and the
+// time-ordered stack plan of pushes per step (see the device comment).
+bool plan_bridge(uint32_t N, BridgePlanHost &out)
+{
+    if (N == 0 || N > kQmcMaxSteps) return false;
+    struct Node { uint32_t m, l, r; };
+    std::vector<Node> nodes;
+    std::map<std::pair<uint32_t, uint32_t>, int> node_of;   // interval -> node index
+    nodes.push_back({N, 0, N});
+    std::deque<std::pair<uint32_t, uint32_t>> queue;
+    queue.push_back({0, N});
+    while (!queue.empty()) {
+        const auto iv = queue.front();
+        queue.pop_front();
+        if (iv.second - iv.first < 2) continue;
+        const uint32_t m = iv.first + (iv.second - iv.first) / 2;
+        node_of[iv] = (int)nodes.size();
+        nodes.push_back({m, iv.first, iv.second});
+        queue.push_back({iv.first, m});
+        queue.push_back({m, iv.second});
+    }
+    if (nodes.size() != N) return false;
+    out.N = N;
+    out.depth = 0;
+    out.ev.clear();
+    out.off.assign(N + 1, 0);
+    std::vector<uint32_t> right;            // right ends of the open intervals (stack)
+    for (uint32_t k = 0; k < N; ++k) {
+        out.off[k] = (int32_t)out.ev.size();
+        if (k == 0) {
+            out.ev.push_back({0, 0.0f, (float)std::sqrt((double)N), 0});
+            right.push_back(N);
+        }
+        uint32_t r = right.back();
+        while (r - k >= 2) {
+            const auto it = node_of.find({k, r});
+            if (it == node_of.end()) return false;
+            const double m = nodes[it->second].m;
+            out.ev.push_back({it->second, (float)((m - k) / (double)(r - k)),
+                              (float)std::sqrt((m - k) * (r - m) / (double)(r - k)), 0});
+            right.push_back((uint32_t)m);
+            r = (uint32_t)m;
+        }
+        if (r != k + 1) return false;
+        if ((int)right.size() > out.depth) out.depth = (int)right.size();
+        if (out.depth >= kQmcMaxLevels) return false;
+        right.pop_back();
+    }
+    out.off[N] = (int32_t)out.ev.size();
+    return true;
+}
+
+struct QmcLayout {
+    size_t off_V, off_T, off_evoff, off_ev, total;
+};
+
+QmcLayout qmc_layout(uint32_t N, size_t n_ev)
+{
+    const size_t D = 2u * (size_t)N;
+    QmcLayout L;
+    L.off_V = 0;
+    L.off_T = align256(L.off_V + D * 32 * sizeof(uint32_t));
+    L.off_evoff = align256(L.off_T + D * 64 * sizeof(uint32_t));
+    L.off_ev = align256(L.off_evoff + (N + 1) * sizeof(int32_t));
+    L.total = align256(L.off_ev + n_ev * sizeof(BridgeOp));
+    return L;
+}
+
+QmcTables qmc_tables_at(const void *base, const QmcLayout &L)
+{
+    const char *b = (const char *)base;
+    return QmcTables{(const uint32_t *)(b + L.off_V), (const uint32_t *)(b + L.off_T),
+                     (const BridgeOp *)(b + L.off_ev), (const int32_t *)(b + L.off_evoff)};
+}
+
+// QMC workspace: tile rows | replicate sums | U [tpr][D] | shifts [R][D].
+struct QmcWs {
+    size_t off_rows, off_rep, off_U, off_shift, total;
+};
+
+QmcWs qmc_ws_layout(uint32_t nc, uint64_t n_paths, uint32_t N, uint32_t R)
+{
+    const size_t w = 12u * nc * sizeof(double);
+    const uint64_t tiles = tiles_for(n_paths);
+    const uint64_t tpr = tiles / R;
+    const size_t D = 2u * (size_t)N;
+    QmcWs L;
+    L.off_rows = 0;
+    L.off_rep = align256(tiles * w);
+    L.off_U = L.off_rep + align256((size_t)R * w);
+    L.off_shift = L.off_U + align256(tpr * D * sizeof(uint32_t));
+    L.total = L.off_shift + align256((size_t)R * D * sizeof(uint32_t));
+    return L;
+}
+
+int validate_qmc(uint64_t n_paths, uint32_t N, const Prepared &pp)
+{
+    if (pp.opt.prec != HESTON_FP32) return HESTON_ERR_UNSUPPORTED;
+    const uint32_t R = pp.opt.n_shifts;
+    if (R < 2 || n_paths % R) return HESTON_ERR_INVALID_ARG;
+    const uint64_t ppr = n_paths / R;
+    if (ppr % kTile || ppr > (1ull << 32)) return HESTON_ERR_INVALID_ARG;
+    if (N > kQmcMaxSteps) return HESTON_ERR_UNSUPPORTED;
+    return HESTON_OK;
+}
+
+template <int TRUNC, int MON>
+cudaError_t launch_qmc_t(const Prepared &pp, const QmcLaunch &a, cudaStream_t st)
+{
+    auto kern = heston_qmc_kernel<TRUNC, MON>;
+    int dev = 0, n_sm = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPathBlock, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    uint64_t grid = pp.opt.grid_ctas ? pp.opt.grid_ctas
+                                     : std::min<uint64_t>((a.n_tiles + 3) / 4, (uint64_t)n_sm * per_sm);
+    if (grid < 1) grid = 1;
+    const int block = pp.opt.block_threads ? (int)pp.opt.block_threads : kPathBlock;
+    kern<<<(unsigned)grid, block, 0, st>>>(pp.kf, pp.csf, a);
+    return cudaGetLastError();
+}
+
+int enqueue_qmc(const Prepared &pp, uint64_t n_paths, uint64_t seed, const void *d_tables,
+                void *ws, size_t ws_bytes, double *d_out, cudaStream_t st)
+{
+    BridgePlanHost plan;
+    if (!plan_bridge(pp.N, plan)) return HESTON_ERR_UNSUPPORTED;
+    const QmcLayout TL = qmc_layout(pp.N, plan.ev.size());
+    const uint32_t R = pp.opt.n_shifts;
+    const QmcWs WL = qmc_ws_layout(pp.cs.n, n_paths, pp.N, R);
+    if (!d_tables || ((uintptr_t)d_tables & 255u)) return HESTON_ERR_INVALID_ARG;
+    if (!ws || ((uintptr_t)ws & 255u) || ws_bytes < WL.total || !d_out) return HESTON_ERR_WORKSPACE;
+    char *b = (char *)ws;
+    QmcLaunch a;
+    a.tb = qmc_tables_at(d_tables, TL);
+    a.D = 2u * pp.N;
+    a.N = pp.N;
+    a.n_tiles = tiles_for(n_paths);
+    a.tpr = (uint32_t)(a.n_tiles / R);
+    a.tile_sums = (double *)(b + WL.off_rows);
+    uint32_t *U = (uint32_t *)(b + WL.off_U);
+    uint32_t *shift = (uint32_t *)(b + WL.off_shift);
+    a.U = U;
+    a.shift = shift;
+    const uint64_t n_setup = (uint64_t)a.tpr * a.D + (uint64_t)R * a.D;
+    qmc_setup_kernel<<<(unsigned)((n_setup + 255) / 256), 256, 0, st>>>(a.tb.V, a.D, a.tpr, R,
+                                                                       key_of(seed), U, shift);
+    if (cudaGetLastError() != cudaSuccess) return HESTON_ERR_CUDA;
+    const int mon = mon_mode(pp.cs);
+    const bool full = pp.opt.trunc == HESTON_TRUNC_FULL;
+    cudaError_t e;
+    if (full) e = mon == MON_NONE ? launch_qmc_t<0, MON_NONE>(pp, a, st)
+                : mon == MON_EVERY ? launch_qmc_t<0, MON_EVERY>(pp, a, st) : launch_qmc_t<0, MON_STRIDE>(pp, a, st);
+    else      e = mon == MON_NONE ? launch_qmc_t<1, MON_NONE>(pp, a, st)
+                : mon == MON_EVERY ? launch_qmc_t<1, MON_EVERY>(pp, a, st) : launch_qmc_t<1, MON_STRIDE>(pp, a, st);
+    if (e != cudaSuccess) return HESTON_ERR_CUDA;
+    const int width = 12 * pp.cs.n;
+    double *rep = (double *)(b + WL.off_rep);
+    reduce_replicates_kernel<<<R, 128, 0, st>>>(a.tile_sums, a.tpr, width, rep);
+    if (cudaGetLastError() != cudaSuccess) return HESTON_ERR_CUDA;
+    reduce_final_qmc_kernel<<<1, 128, 0, st>>>(rep, R, pp.cs.n, (double)(n_paths / R),
+                                               pp.gamma_nan ? 1 : 0, d_out);
+    return cudaGetLastError() == cudaSuccess ? HESTON_OK : HESTON_ERR_CUDA;
+}
+
+// Build the tables on the host and copy them to d_tables (synchronous).
+int build_qmc_tables(uint32_t N, void *d_tables, size_t bytes)
+{
+    BridgePlanHost plan;
+    if (!plan_bridge(N, plan)) return HESTON_ERR_UNSUPPORTED;
+    const QmcLayout L = qmc_layout(N, plan.ev.size());
+    if (!d_tables || ((uintptr_t)d_tables & 255u) || bytes < L.total) return HESTON_ERR_WORKSPACE;
+    const uint32_t D = 2u * N;
+    std::vector<unsigned char> h(L.total, 0);
+    uint32_t *V = (uint32_t *)(h.data() + L.off_V);
+    uint32_t *T = (uint32_t *)(h.data() + L.off_T);
+    sobol_directions_host(D, V);
+    for (uint32_t d = 0; d < D; ++d)
+        for (uint32_t p = 0; p < 64; ++p) {
+            uint32_t x = 0;
+            for (int b = 0; b < 6; ++b)
+                if ((p >> b) & 1u) x ^= V[d * 32u + b];
+            T[d * 64u + p] = x;
+        }
+    std::memcpy(h.data() + L.off_evoff, plan.off.data(), plan.off.size() * sizeof(int32_t));
+    std::memcpy(h.data() + L.off_ev, plan.ev.data(), plan.ev.size() * sizeof(BridgeOp));
+    if (cudaMemcpy(d_tables, h.data(), L.total, cudaMemcpyHostToDevice) != cudaSuccess) return HESTON_ERR_CUDA;
+    return HESTON_OK;
+}
+
 }  // namespace
 
 // Static device scratch of heston_mc_launch_noalloc (see include/heston_mc.h):
@@ -822,6 +1413,42 @@ int noalloc_scratch(void **out)
     }
     *out = g_noalloc_ptr[dev];
     return HESTON_OK;
+}
+}  // namespace
+
+namespace {
+// Synchronous randomised-QMC estimate: tables, workspace and output are
+// allocated stream-ordered for this call and freed before it returns.
+int qmc_price_sync(const Prepared &pp, uint64_t n_paths, uint64_t seed, heston_result *out)
+{
+    int rc = validate_qmc(n_paths, pp.N, pp);
+    if (rc < 0) return rc;
+    BridgePlanHost plan;
+    if (!plan_bridge(pp.N, plan)) return HESTON_ERR_UNSUPPORTED;
+    DeviceGuard g(pp.opt.device);
+    if (g.err != cudaSuccess) return HESTON_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)pp.opt.cuda_stream;
+    const size_t tb = qmc_layout(pp.N, plan.ev.size()).total;
+    const size_t wb = qmc_ws_layout(pp.cs.n, n_paths, pp.N, pp.opt.n_shifts).total;
+    const size_t ob = 12u * pp.cs.n * sizeof(double);
+    char *buf = nullptr;
+    if (cudaMallocAsync((void **)&buf, tb + wb + align256(ob), st) != cudaSuccess) {
+        cudaGetLastError();
+        return HESTON_ERR_NOMEM;
+    }
+    int e = cudaStreamSynchronize(st) == cudaSuccess ? HESTON_OK : HESTON_ERR_CUDA;
+    if (e == HESTON_OK) e = build_qmc_tables(pp.N, buf, tb);
+    double *d_out = (double *)(buf + tb + wb);
+    double h[12 * kMaxC];
+    if (e == HESTON_OK) e = enqueue_qmc(pp, n_paths, seed, buf, buf + tb, wb, d_out, st);
+    if (e == HESTON_OK && cudaMemcpyAsync(h, d_out, ob, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        e = HESTON_ERR_CUDA;
+    cudaFreeAsync(buf, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) e = HESTON_ERR_CUDA;
+    if (e < 0) return e;
+    const int status = pp.gamma_nan ? HESTON_WARN_GAMMA_UNDEFINED : HESTON_OK;
+    fill_results(h, (uint32_t)pp.cs.n, n_paths, status, out);
+    return status;
 }
 }  // namespace
 
@@ -863,6 +1490,7 @@ int heston_mc_launch(const heston_params *params, const heston_contract *contrac
     Prepared pp;
     int rc = validate_and_prepare(params, contracts, n_contracts, n_paths, n_steps, opts, pp);
     if (rc < 0) return rc;
+    if (pp.opt.rng != HESTON_RNG_PHILOX) return HESTON_ERR_UNSUPPORTED;
     DeviceGuard g(pp.opt.device);
     if (g.err != cudaSuccess) return HESTON_ERR_CUDA;
     const int e = enqueue(pp, n_paths, rng_seed, d_workspace, workspace_bytes_, d_out,
@@ -878,6 +1506,7 @@ int heston_mc_launch_noalloc(const heston_params *params, const heston_contract 
     Prepared pp;
     int rc = validate_and_prepare(params, contracts, n_contracts, n_paths, n_steps, opts, pp);
     if (rc < 0) return rc;
+    if (pp.opt.rng != HESTON_RNG_PHILOX) return HESTON_ERR_UNSUPPORTED;
     if (!d_out) return HESTON_ERR_INVALID_ARG;
     if (workspace_bytes(n_contracts, n_paths) > (size_t)HESTON_NOALLOC_SCRATCH_BYTES)
         return HESTON_ERR_WORKSPACE;
@@ -901,6 +1530,12 @@ int heston_mc_price_greeks_ex(const heston_params *params, const heston_contract
     int rc = validate_and_prepare(params, contracts, n_contracts, n_paths, n_steps, opts, pp);
     if (rc < 0) {
         for (uint32_t c = 0; c < n_contracts && c < (uint32_t)kMaxC; ++c) out[c].status = rc;
+        return rc;
+    }
+    if (pp.opt.rng == HESTON_RNG_SOBOL_BB) {
+        rc = qmc_price_sync(pp, n_paths, rng_seed, out);
+        if (rc < 0)
+            for (uint32_t c = 0; c < n_contracts; ++c) out[c].status = rc;
         return rc;
     }
     DeviceGuard g(pp.opt.device);
@@ -947,6 +1582,7 @@ int heston_mc_launch_tiles(const heston_params *params, const heston_contract *c
     int rc = validate_and_prepare(params, contracts, n_contracts, n_paths < 2 ? 2 : n_paths,
                                   n_steps, opts, pp);
     if (rc < 0) return rc;
+    if (pp.opt.rng != HESTON_RNG_PHILOX) return HESTON_ERR_UNSUPPORTED;
     if (n_paths == 0 || !d_tile_sums || (path_begin % kTile) != 0) return HESTON_ERR_INVALID_ARG;
     DeviceGuard g(pp.opt.device);
     if (g.err != cudaSuccess) return HESTON_ERR_CUDA;
@@ -986,6 +1622,7 @@ int heston_mc_debug_paths(const heston_params *params, const heston_contract *co
     Prepared pp;
     int rc = validate_and_prepare(params, contracts, n_contracts, 2, n_steps, opts, pp);
     if (rc < 0) return rc;
+    if (pp.opt.rng != HESTON_RNG_PHILOX) return HESTON_ERR_UNSUPPORTED;
     if (!paths || count == 0 || !h_records || !h_estimators) return HESTON_ERR_INVALID_ARG;
     DeviceGuard g(pp.opt.device);
     if (g.err != cudaSuccess) return HESTON_ERR_CUDA;
@@ -1061,6 +1698,123 @@ int heston_rng_debug(uint64_t rng_seed, const uint64_t *paths, const uint32_t *s
         e = HESTON_ERR_CUDA;
     cudaFree(buf);
     return e;
+}
+
+int heston_sobol_directions(uint32_t n_dims, uint32_t *h_out)
+{
+    if (!h_out || n_dims == 0 || n_dims > 2 * kQmcMaxSteps) return HESTON_ERR_INVALID_ARG;
+    sobol_directions_host(n_dims, h_out);
+    return HESTON_OK;
+}
+
+int heston_qmc_tables_bytes(uint32_t n_steps, size_t *bytes)
+{
+    if (!bytes || n_steps == 0) return HESTON_ERR_INVALID_ARG;
+    BridgePlanHost plan;
+    if (!plan_bridge(n_steps, plan)) return HESTON_ERR_UNSUPPORTED;
+    *bytes = qmc_layout(n_steps, plan.ev.size()).total;
+    return HESTON_OK;
+}
+
+int heston_qmc_build_tables(uint32_t n_steps, void *d_tables, size_t bytes, int32_t device)
+{
+    if (n_steps == 0) return HESTON_ERR_INVALID_ARG;
+    DeviceGuard g(device);
+    if (g.err != cudaSuccess) return HESTON_ERR_CUDA;
+    return build_qmc_tables(n_steps, d_tables, bytes);
+}
+
+int heston_mc_workspace_bytes_qmc(uint32_t n_contracts, uint64_t n_paths, uint32_t n_steps,
+                                  uint32_t n_shifts, size_t *bytes)
+{
+    if (!bytes || n_contracts == 0 || n_contracts > (uint32_t)kMaxC || n_steps == 0 ||
+        n_steps > kQmcMaxSteps || n_shifts < 2 || n_paths % n_shifts ||
+        (n_paths / n_shifts) % kTile || n_paths / n_shifts > (1ull << 32))
+        return HESTON_ERR_INVALID_ARG;
+    *bytes = qmc_ws_layout(n_contracts, n_paths, n_steps, n_shifts).total;
+    return HESTON_OK;
+}
+
+int heston_mc_launch_qmc(const heston_params *params, const heston_contract *contracts,
+                         uint32_t n_contracts, uint64_t n_paths, uint32_t n_steps, uint64_t rng_seed,
+                         const heston_options *opts, const void *d_tables, void *d_workspace,
+                         size_t workspace_bytes_, double *d_out)
+{
+    Prepared pp;
+    int rc = validate_and_prepare(params, contracts, n_contracts, n_paths, n_steps, opts, pp);
+    if (rc < 0) return rc;
+    if (pp.opt.rng != HESTON_RNG_SOBOL_BB) return HESTON_ERR_INVALID_ARG;
+    rc = validate_qmc(n_paths, n_steps, pp);
+    if (rc < 0) return rc;
+    DeviceGuard g(pp.opt.device);
+    if (g.err != cudaSuccess) return HESTON_ERR_CUDA;
+    const int e = enqueue_qmc(pp, n_paths, rng_seed, d_tables, d_workspace, workspace_bytes_, d_out,
+                              (cudaStream_t)pp.opt.cuda_stream);
+    if (e < 0) return e;
+    return pp.gamma_nan ? HESTON_WARN_GAMMA_UNDEFINED : HESTON_OK;
+}
+
+int heston_qmc_debug_paths(const heston_params *params, const heston_contract *contracts,
+                           uint32_t n_contracts, uint32_t n_steps, uint64_t rng_seed,
+                           const heston_options *opts, uint32_t replicate, const uint32_t *points,
+                           uint32_t count, double *h_records, double *h_estimators)
+{
+    Prepared pp;
+    int rc = validate_and_prepare(params, contracts, n_contracts, 2, n_steps, opts, pp);
+    if (rc < 0) return rc;
+    if (pp.opt.rng != HESTON_RNG_SOBOL_BB || !points || count == 0 || !h_records || !h_estimators ||
+        replicate >= (1u << 16))
+        return HESTON_ERR_INVALID_ARG;
+    if (pp.opt.prec != HESTON_FP32 || n_steps > kQmcMaxSteps) return HESTON_ERR_UNSUPPORTED;
+    BridgePlanHost plan;
+    if (!plan_bridge(n_steps, plan)) return HESTON_ERR_UNSUPPORTED;
+    DeviceGuard g(pp.opt.device);
+    if (g.err != cudaSuccess) return HESTON_ERR_CUDA;
+    const uint32_t D = 2u * n_steps;
+    const QmcLayout TL = qmc_layout(n_steps, plan.ev.size());
+    const size_t pb = align256(sizeof(uint32_t) * count);
+    const size_t ub = align256(sizeof(uint32_t) * (size_t)count * D);
+    const size_t sb = align256(sizeof(uint32_t) * (size_t)(replicate + 1) * D);
+    const size_t rb = align256(sizeof(double) * kRecordDoubles * count);
+    const size_t eb = align256(sizeof(double) * 6 * n_contracts * (size_t)count);
+    char *buf = nullptr;
+    if (cudaMalloc((void **)&buf, TL.total + pb + ub + sb + rb + eb) != cudaSuccess) {
+        cudaGetLastError();
+        return HESTON_ERR_NOMEM;
+    }
+    char *p = buf + TL.total;
+    uint32_t *dp = (uint32_t *)p;         p += pb;
+    uint32_t *dU = (uint32_t *)p;         p += ub;
+    uint32_t *dS = (uint32_t *)p;         p += sb;
+    double *dr = (double *)p;             p += rb;
+    double *de = (double *)p;
+    int e = build_qmc_tables(n_steps, buf, TL.total);
+    if (e == HESTON_OK && cudaMemcpy(dp, points, sizeof(uint32_t) * count, cudaMemcpyHostToDevice) != cudaSuccess)
+        e = HESTON_ERR_CUDA;
+    if (e == HESTON_OK) {
+        const QmcTables tb = qmc_tables_at(buf, TL);
+        const uint64_t nu = (uint64_t)count * D;
+        qmc_debug_high_bits_kernel<<<(unsigned)((nu + 255) / 256), 256>>>(tb.V, D, dp, count, dU);
+        const uint64_t ns = (uint64_t)(replicate + 1) * D;
+        qmc_setup_kernel<<<(unsigned)((ns + 255) / 256), 256>>>(tb.V, D, 0, replicate + 1,
+                                                                 key_of(rng_seed), nullptr, dS);
+        const uint32_t *srow = dS + (uint64_t)replicate * D;
+        const unsigned grid = (count + 127) / 128;
+        const int mon = mon_mode(pp.cs);
+        const bool full = pp.opt.trunc == HESTON_TRUNC_FULL;
+#define HESTON_QDBG(TR, MO) heston_qmc_debug_kernel<TR, MO><<<grid, 128>>>(pp.kf, pp.csf, tb, n_steps, dp, dU, srow, count, dr, de)
+        if (full) { if (mon == MON_NONE) HESTON_QDBG(0, MON_NONE); else if (mon == MON_EVERY) HESTON_QDBG(0, MON_EVERY); else HESTON_QDBG(0, MON_STRIDE); }
+        else      { if (mon == MON_NONE) HESTON_QDBG(1, MON_NONE); else if (mon == MON_EVERY) HESTON_QDBG(1, MON_EVERY); else HESTON_QDBG(1, MON_STRIDE); }
+#undef HESTON_QDBG
+        if (cudaGetLastError() != cudaSuccess) e = HESTON_ERR_CUDA;
+    }
+    if (e == HESTON_OK &&
+        (cudaMemcpy(h_records, dr, sizeof(double) * kRecordDoubles * count, cudaMemcpyDeviceToHost) != cudaSuccess ||
+         cudaMemcpy(h_estimators, de, sizeof(double) * 6 * n_contracts * (size_t)count, cudaMemcpyDeviceToHost) != cudaSuccess))
+        e = HESTON_ERR_CUDA;
+    cudaFree(buf);
+    if (e < 0) return e;
+    return pp.gamma_nan ? HESTON_WARN_GAMMA_UNDEFINED : HESTON_OK;
 }
 
 }  // extern "C"

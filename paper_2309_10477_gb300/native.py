@@ -101,6 +101,15 @@ def load():
                                    P(ctypes.c_double)], i32),
         "heston_rng_debug": ([u64, P(u64), P(u32), u32, i32, P(u32), P(ctypes.c_double)], i32),
         "heston_status_string": ([ctypes.c_int], ctypes.c_char_p),
+        "heston_sobol_directions": ([u32, P(u32)], i32),
+        "heston_qmc_tables_bytes": ([u32, P(sz)], i32),
+        "heston_qmc_build_tables": ([u32, vp, sz, i32], i32),
+        "heston_mc_workspace_bytes_qmc": ([u32, u64, u32, u32, P(sz)], i32),
+        "heston_mc_launch_qmc": ([P(heston_params), P(heston_contract), u32, u64, u32, u64,
+                                  P(heston_options), vp, vp, sz, vp], i32),
+        "heston_qmc_debug_paths": ([P(heston_params), P(heston_contract), u32, u32, u64,
+                                    P(heston_options), u32, P(u32), u32, P(ctypes.c_double),
+                                    P(ctypes.c_double)], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -246,3 +255,50 @@ def results_to_arrays(results):
     m = np.array([[getattr(r, k) for k in ESTIMATORS] for r in results])
     se = np.array([list(r.se) for r in results])
     return m, se
+
+
+def heston_sobol_directions(n_dims: int) -> np.ndarray:
+    """Direction integers built by the library's host code: (n_dims, 32) uint32."""
+    out = np.zeros((n_dims, 32), dtype=np.uint32)
+    _check(load().heston_sobol_directions(n_dims, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))))
+    return out
+
+
+def heston_qmc_tables_bytes(n_steps: int) -> int:
+    b = ctypes.c_size_t()
+    _check(load().heston_qmc_tables_bytes(n_steps, ctypes.byref(b)))
+    return b.value
+
+
+def heston_qmc_build_tables(n_steps: int, tables, nbytes: int, device: int = -1) -> int:
+    return _check(load().heston_qmc_build_tables(n_steps, _ptr(tables), nbytes, device))
+
+
+def heston_mc_workspace_bytes_qmc(n_contracts, n_paths, n_steps, n_shifts) -> int:
+    b = ctypes.c_size_t()
+    _check(load().heston_mc_workspace_bytes_qmc(n_contracts, n_paths, n_steps, n_shifts,
+                                                ctypes.byref(b)))
+    return b.value
+
+
+def heston_mc_launch_qmc(params, contracts, n_paths, n_steps, rng_seed, options, tables,
+                         workspace, workspace_bytes, out) -> int:
+    cs = _contract_array(contracts)
+    return _check(load().heston_mc_launch_qmc(ctypes.byref(params), cs, len(contracts), n_paths,
+                                              n_steps, rng_seed, ctypes.byref(options),
+                                              _ptr(tables), _ptr(workspace), workspace_bytes,
+                                              _ptr(out)))
+
+
+def heston_qmc_debug_paths(params, contracts, n_steps, rng_seed, options, replicate, points):
+    points = np.ascontiguousarray(np.asarray(points, dtype=np.uint32))
+    n = len(points)
+    rec = np.zeros((n, len(RECORD_FIELDS)))
+    est = np.zeros((n, len(contracts), 6))
+    cs = _contract_array(contracts)
+    D = ctypes.POINTER(ctypes.c_double)
+    _check(load().heston_qmc_debug_paths(ctypes.byref(params), cs, len(contracts), n_steps,
+                                         rng_seed, ctypes.byref(options), replicate,
+                                         points.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
+                                         n, rec.ctypes.data_as(D), est.ctypes.data_as(D)))
+    return rec, est

@@ -1,0 +1,118 @@
+"""GPU randomised-QMC variant (Sobol + digital shifts + Brownian bridge) vs
+the FP64 oracle's independent implementation, through the C ABI.  Same
+tolerances as the Philox parity tests (per path 1e-5 relative in FP32,
+branch flips counted; estimates within 3 SE and 1e-4 * max(1, |oracle|))."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import sobol
+from paper_2309_10477_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+BASE = wl.BASE_PARAMS
+
+
+@pytest.fixture(scope="module")
+def nv(cuda_lib):
+    from paper_2309_10477_gb300 import native
+    return native
+
+
+def _oc(cs):
+    return [oracle.Contract(*c) for c in cs]
+
+
+def _gc(nv, cs):
+    return [nv.make_contract(*c) for c in cs]
+
+
+def _flips(rec, cs, params, N):
+    near_zero = rec[:, 14] < 1e-5 * max(params["theta"], params["v0"])
+    A_euro = params["S0"] * np.exp(rec[:, 0])
+    near_k = np.zeros(len(rec), bool)
+    for c in cs:
+        M = c[4] or N
+        A = A_euro if c[0] == 0 else rec[:, 6] / M
+        near_k |= np.abs(A - c[1]) < 2e-5 * max(c[1], 1.0)
+    return near_zero | near_k
+
+
+@pytest.mark.parametrize("N,trunc", [(1, 0), (7, 0), (64, 0), (252, 0), (64, 1)])
+def test_qmc_per_path(nv, N, trunc):
+    cs = [(0, 100.0, 1.0, 0, 0), (1, 95.0, 1.0, 0, 0), (0, 105.0, 1.0, 1, 0)]
+    rep = 3
+    pts = np.concatenate([np.arange(0, 300), [4095, 4096, 123457, 2**20 + 77, 2**31 + 5]])
+    opts = nv.make_options(trunc=trunc, prec=nv.HESTON_FP32, rng=nv.HESTON_RNG_SOBOL_BB, n_shifts=4)
+    rec_g, est_g = nv.heston_qmc_debug_paths(nv.make_params(**BASE), _gc(nv, cs), N, 42, opts, rep, pts)
+    V = sobol.direction_numbers(2 * N)
+    za, zb = sobol.qmc_normals(V, sobol.BridgePlan(N), 42, rep, pts)
+    rec_o, est_o = oracle.paths_from_normals(oracle.Params(**BASE), _oc(cs), za, zb, trunc)
+    ok = ~_flips(rec_o, cs, BASE, N)
+    assert (~ok).sum() <= 2
+    X_g, X_o = rec_g[ok, 0], rec_o[ok, 0]
+    assert (np.abs(X_g - X_o) <= 1e-5 * np.maximum(1.0, np.abs(X_o))).all(), np.abs(X_g - X_o).max()
+    vs = np.maximum(np.abs(rec_o[ok, 1]), max(BASE["theta"], BASE["v0"]))
+    assert (np.abs(rec_g[ok, 1] - rec_o[ok, 1]) <= 1e-5 * vs).all()
+    assert (np.abs(rec_g[ok, 6] - rec_o[ok, 6]) <= 1e-5 * np.abs(rec_o[ok, 6])).all()
+    for ci, c in enumerate(cs):
+        A = np.maximum(c[1], np.abs(est_o[ok, ci, 1]) * BASE["S0"])
+        assert (np.abs(est_g[ok, ci, 0] - est_o[ok, ci, 0]) <= 1e-5 * A).all()
+
+
+@pytest.mark.parametrize("N,P,R", [(50, 4096, 8), (252, 1024, 4)])
+def test_qmc_estimates_match_oracle(nv, N, P, R):
+    cs = [(0, 90.0, 1.0, 0, 0), (0, 110.0, 1.0, 0, 0), (1, 100.0, 1.0, 0, 0), (1, 100.0, 1.0, 1, 0)]
+    opts = nv.make_options(prec=nv.HESTON_FP32, rng=nv.HESTON_RNG_SOBOL_BB, n_shifts=R)
+    res = nv.heston_mc_price_greeks_ex(nv.make_params(**BASE), _gc(nv, cs), R * P, N, 9, opts)
+    gm, gse = nv.results_to_arrays(res)
+    om, ose, _ = sobol.qmc_price_greeks(oracle.Params(**BASE), _oc(cs), R, P, N, 9)
+    d = np.abs(gm - om)
+    assert (d <= 3 * ose + 1e-12).all(), np.max(d / (ose + 1e-300))
+    assert (d <= 1e-4 * np.maximum(1.0, np.abs(om))).all()
+    np.testing.assert_allclose(gse, ose, rtol=2e-2, atol=1e-6)
+
+
+def test_qmc_async_launch_matches_sync_and_full_size_runs(nv):
+    import torch
+    w = wl.multi_strike_fp32()
+    cs = _gc(nv, w.contracts)
+    R, N = 32, w.n_steps
+    params = nv.make_params(**w.params)
+    tb_bytes = nv.heston_qmc_tables_bytes(N)
+    tables = torch.empty(tb_bytes // 8 + 1, dtype=torch.float64, device="cuda")
+    nv.heston_qmc_build_tables(N, tables, tb_bytes)
+    for n in (R * 2048, w.n_paths):
+        ws_bytes = nv.heston_mc_workspace_bytes_qmc(len(cs), n, N, R)
+        ws = torch.empty(ws_bytes // 8 + 1, dtype=torch.float64, device="cuda")
+        out = torch.empty(len(cs) * 12, dtype=torch.float64, device="cuda")
+        opts = nv.make_options(prec=nv.HESTON_FP32, rng=nv.HESTON_RNG_SOBOL_BB, n_shifts=R,
+                               stream=torch.cuda.current_stream())
+        nv.heston_mc_launch_qmc(params, cs, n, N, w.seed, opts, tables, ws, ws_bytes, out)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy().reshape(len(cs), 12)
+        assert np.isfinite(got).all()
+        if n < w.n_paths:
+            sync = nv.results_to_arrays(nv.heston_mc_price_greeks_ex(params, cs, n, N, w.seed, opts))
+            assert np.array_equal(got[:, :6], sync[0]) and np.array_equal(got[:, 6:], sync[1])
+    # full size: QMC and Philox MC agree within their combined standard errors
+    mc = nv.results_to_arrays(nv.heston_mc_price_greeks_ex(
+        params, cs, w.n_paths, N, w.seed, nv.make_options(prec=nv.HESTON_FP32)))
+    d = np.abs(got[:, :6] - mc[0])
+    assert (d <= 4 * np.hypot(got[:, 6:], mc[1]) + 1e-9).all()
+    assert (got[:, 6] < mc[1][:, 0]).all()       # price SE: bridge-QMC below Philox MC
+
+
+def test_qmc_rejections(nv):
+    p = nv.make_params(**BASE)
+    cs = [nv.make_contract(0, 100.0, 1.0)]
+    with pytest.raises(nv.HestonError) as e:
+        nv.heston_mc_price_greeks_ex(p, cs, 4096, 16, 1, nv.make_options(
+            prec=nv.HESTON_FP64, rng=nv.HESTON_RNG_SOBOL_BB, n_shifts=4))
+    assert e.value.status == nv.HESTON_ERR_UNSUPPORTED
+    for n_paths, n_shifts in ((4096, 1), (4096 + 64, 3), (4096 * 3 + 3, 3)):
+        with pytest.raises(nv.HestonError) as e:
+            nv.heston_mc_price_greeks_ex(p, cs, n_paths, 16, 1, nv.make_options(
+                prec=nv.HESTON_FP32, rng=nv.HESTON_RNG_SOBOL_BB, n_shifts=n_shifts))
+        assert e.value.status == nv.HESTON_ERR_INVALID_ARG
