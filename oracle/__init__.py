@@ -12,6 +12,9 @@ Contents:
     price and Greeks (the "real price" the paper quotes in Sec. 3).
   * ``sobol`` -- Sobol points, digital shifts, inverse normal and Brownian
     bridge for the randomised quasi-Monte Carlo variant (Sec. 2.7).
+  * ``exact`` -- Broadie-Kaya exact simulation (Sec. 2.2-2.3): noncentral
+    chi-square variance step, integrated variance by Fourier inversion of its
+    conditional CDF, conditional log-price.
 
 Parity pins live in ``tests/test_oracle_*.py``; functions with no pin say
 "parity unpinned" in their docstring.
