@@ -321,6 +321,77 @@ def run_gpu(args):
                "path_steps_per_s_at_philox_se": n * w.n_steps / (q_ms * 1e-3) / se_ratio**2,
                "gpu_launches_per_step": 4}
 
+    # batched form: 1024 uneven contracts in one persistent launch (captured in a
+    # CUDA graph) against one launch per contract, same paths hence same SE
+    batched = None
+    if not args.no_batch and world == 1:
+        from paper_2309_10477_gb300 import autotune
+        bitems = [nv.make_batch_item(nv.make_params(**d["params"]), nv.make_contract(*d["contract"]),
+                                     d["n_paths"], d["n_steps"], w.seed + 1000003 * i)
+                  for i, d in enumerate(wl.batched_contracts(1024))]
+        bopts = nv.make_options(prec=nv.HESTON_FP32, stream=stream, device=local)
+        plan = nv.heston_batch_plan_make(bitems, bopts)
+        desc = torch.empty(plan.descriptor_bytes // 8 + 32, dtype=torch.float64, device=dev)
+        bws = torch.empty(plan.workspace_bytes // 8 + 32, dtype=torch.float64, device=dev)
+        bout = torch.empty(len(bitems) * 12, dtype=torch.float64, device=dev)
+        nv.heston_batch_prepare(bitems, bopts, plan, desc)
+        (blk, grd), tune_ms = autotune.tune_batch(plan, desc, bws, bout, bopts, stream=stream)
+        topts = nv.make_options(prec=nv.HESTON_FP32, stream=stream, device=local,
+                                block_threads=blk, grid_ctas=grd)
+        gstream = torch.cuda.Stream(device=dev)
+        gstream.wait_stream(stream)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=gstream):
+            gopts = nv.make_options(prec=nv.HESTON_FP32, stream=torch.cuda.current_stream(),
+                                    device=local, block_threads=blk, grid_ctas=grd)
+            nv.heston_mc_launch_batch(plan, desc, gopts, bws, bout)
+        graph.replay()
+        barrier()
+        b_steps = max(3, min(args.steps // 20, 10))
+        clocks.mark(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(b_steps):
+            graph.replay()
+        e1.record(stream)
+        barrier()
+        batch_ms = e0.elapsed_time(e1) / b_steps
+        # one launch per contract, each with its own workspace slice, back to back
+        single = []
+        for it in bitems:
+            sb = nv.heston_mc_workspace_bytes(1, it.n_paths)
+            single.append((it, sb))
+        sws = torch.empty(max(sb for _, sb in single) // 8 + 32, dtype=torch.float64, device=dev)
+        sout = torch.empty(len(bitems) * 12, dtype=torch.float64, device=dev)
+        def per_contract():
+            for i, (it, sb) in enumerate(single):
+                nv.heston_mc_launch(it.params, [it.contract], it.n_paths, it.n_steps, it.rng_seed,
+                                    bopts, sws, sb, sout[i * 12:(i + 1) * 12])
+        per_contract()
+        barrier()
+        e0.record(stream)
+        for _ in range(2):
+            per_contract()
+        e1.record(stream)
+        barrier()
+        clocks.mark(False)
+        single_ms = e0.elapsed_time(e1) / 2
+        same = bool(torch.equal(torch.nan_to_num(bout), torch.nan_to_num(sout)))
+        n_unstable = int((~torch.isfinite(bout.view(-1, 12)[:, [3, 5, 9, 11]])).any(dim=1).sum())
+        batched = {"workload": "1024 seeded uneven contracts: K~U[70,130], T in {0.25,0.5,1,2}, "
+                               "paths 2^U (U~U[14,20]), steps 50..500, European/Asian 50/50, FP32",
+                   "total_path_steps": int(plan.total_path_steps),
+                   "batch_ms": batch_ms, "greek_sets_per_s": len(bitems) / (batch_ms * 1e-3),
+                   "path_steps_per_s": plan.total_path_steps / (batch_ms * 1e-3),
+                   "per_contract_ms": single_ms,
+                   "per_contract_greek_sets_per_s": len(bitems) / (single_ms * 1e-3),
+                   "speedup_vs_per_contract": single_ms / batch_ms,
+                   "results_identical_to_per_contract": same,
+                   "contracts_with_unstable_vega_theta": n_unstable,
+                   "launch_shape": {"block_threads": blk, "grid_ctas": grd,
+                                    "tuned_candidates": len(tune_ms)},
+                   "graph": "memset + persistent kernel + 2 reductions captured, replayed"}
+
     # end to end through the synchronous host API (host structs in, results out)
     res_arr = (nv.heston_result * nc)()
     carr = (nv.heston_contract * nc)(*contracts)
@@ -385,6 +456,8 @@ def run_gpu(args):
         }
         if qmc is not None:
             line["qmc_variant"] = qmc
+        if batched is not None:
+            line["batched_variant"] = batched
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
         print(json.dumps(line), flush=True)
@@ -402,6 +475,7 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-qmc", action="store_true", help="skip the quasi-Monte Carlo variant")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched 1024-contract form")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--n-paths", type=int, default=0,
                     help="paths per rank (default: the workload's 2^22); small cases for ncu")

@@ -46,6 +46,7 @@ extern "C" {
 /* ---- status codes ----------------------------------------------------- */
 #define HESTON_OK                    0
 #define HESTON_WARN_GAMMA_UNDEFINED  1  /* |rho| == 1 or v0 == 0: Gamma (and its SE) set to NaN */
+#define HESTON_WARN_TANGENT_UNSTABLE 2  /* a Vega or Theta estimate or SE is not finite (see below) */
 #define HESTON_ERR_INVALID_ARG      -1  /* a parameter is out of its domain (see heston_mc_price_greeks_ex) */
 #define HESTON_ERR_CUDA             -2  /* a CUDA runtime call failed */
 #define HESTON_ERR_NOMEM            -3  /* device allocation failed */
@@ -106,7 +107,16 @@ typedef struct {
     uint32_t reserved;
 } heston_options;
 
-/* Result for one contract: discounted price, Delta = dV/dS0,
+/* Vega and Theta are pathwise tangents through sqrt(V): each step scales the
+ * v0- and T-tangents by about 1 + xi sqrt(dt) Z / (2 sqrt(V)).  When the
+ * variance process comes close to zero (parameters far from the Feller
+ * condition 2 kappa theta >= xi^2, many steps) the per-path tangents have
+ * unbounded variance, the estimates are meaningless and in FP32 may
+ * overflow; the synchronous entry points then return
+ * HESTON_WARN_TANGENT_UNSTABLE (per result in heston_result.status).  Price,
+ * Delta, Gamma and Rho do not use the tangents and are unaffected.
+ *
+ * Result for one contract: discounted price, Delta = dV/dS0,
  * Gamma = d2V/dS0^2, Vega = dV/dv0, Rho = dV/dr, Theta = -dV/dT, and the
  * standard error of each mean (sample stdev / sqrt(n)), se[] in the same
  * order.  The first 12 doubles match the device output layout below. */
@@ -284,6 +294,64 @@ int heston_qmc_debug_paths(const heston_params *params, const heston_contract *c
                            uint32_t n_contracts, uint32_t n_steps, uint64_t rng_seed,
                            const heston_options *opts, uint32_t replicate, const uint32_t *points,
                            uint32_t count, double *h_records, double *h_estimators);
+
+/* ---- batched persistent launch -------------------------------------------- */
+
+/* Many uneven contracts in one launch (the batched form of the paper's
+ * Algorithm "Monte Carlo option pricing estimation", Sec. 2.5): each item
+ * has its own parameters, path count, step count and seed, and its result
+ * equals heston_mc_launch of that item alone (same seed) bit for bit.
+ * Work items are (contract, 64-path tile) pairs taken from a device counter,
+ * contracts with the most steps first, by persistent warps.  FP32 paths
+ * only; trunc from the options, common to the batch. */
+typedef struct {
+    heston_params params;
+    heston_contract contract;
+    uint64_t n_paths;
+    uint32_t n_steps;
+    uint32_t reserved;          /* must be 0 */
+    uint64_t rng_seed;
+} heston_batch_item;
+
+/* Host-side plan of a batch: sizes the caller allocates and the totals the
+ * launch needs.  Filled by heston_batch_plan_make. */
+typedef struct {
+    uint64_t total_tiles;       /* work items */
+    uint64_t total_groups;      /* first-level reduction rows */
+    uint64_t total_path_steps;
+    uint32_t n_items;
+    int32_t trunc;
+    size_t descriptor_bytes;    /* device buffer for heston_batch_prepare */
+    size_t workspace_bytes;     /* device buffer for heston_mc_launch_batch */
+} heston_batch_plan;
+
+/* Validate every item (as heston_mc_price_greeks_ex would; FP32 only) and
+ * size the buffers.  items: host array of n_items (>= 1). */
+int heston_batch_plan_make(const heston_batch_item *items, uint32_t n_items,
+                           const heston_options *opts, heston_batch_plan *plan);
+
+/* Write the device descriptors of the batch (per-contract constants, work
+ * order) into d_desc (device, 256-byte aligned, plan->descriptor_bytes).
+ * Synchronous.  The descriptors are read-only afterwards and serve any
+ * number of launches. */
+int heston_batch_prepare(const heston_batch_item *items, const heston_options *opts,
+                         const heston_batch_plan *plan, void *d_desc);
+
+/* Enqueue the batch on opts->cuda_stream: one memset, the persistent path
+ * kernel and two reduction kernels; no allocation, no synchronisation.
+ * d_workspace: device, 256-byte aligned, plan->workspace_bytes.  d_out:
+ * device, n_items x 12 doubles (layout as heston_mc_launch, one contract per
+ * item).  d_status: optional device int32 (NULL = none): 0 runs the batch;
+ * if it holds 1 the warps take no further work items and set it to 2
+ * (the outputs are then incomplete); the launch never resets it. */
+int heston_mc_launch_batch(const heston_batch_plan *plan, const void *d_desc,
+                           const heston_options *opts, void *d_workspace, double *d_out,
+                           int32_t *d_status);
+
+/* Synchronous convenience: plan, allocate, prepare, launch, copy back.
+ * out: host array of n_items results. */
+int heston_mc_price_greeks_batch(const heston_batch_item *items, uint32_t n_items,
+                                 const heston_options *opts, heston_result *out);
 
 /* ---- test support --------------------------------------------------------- */
 

@@ -762,21 +762,21 @@ __global__ void reduce_final_qmc_kernel(const double *rep_sums, uint32_t R, int 
 // [g*256, (g+1)*256) column by column in tile order.  Level 2: one CTA sums
 // the groups in order and forms mean and standard error per estimator.
 // ---------------------------------------------------------------------------
-__global__ void reduce_groups_kernel(const double *tile_sums, uint64_t n_tiles, int width,
-                                     double *group_sums)
+// Column sums of tile rows [lo, hi) in row order (one group of <= 256 tiles).
+__device__ __forceinline__ void sum_rows(const double *rows, uint64_t lo, uint64_t hi, int width,
+                                         double *out_row)
 {
-    const uint64_t g = blockIdx.x;
-    const uint64_t lo = g * kGroupTiles;
-    const uint64_t hi = lo + kGroupTiles < n_tiles ? lo + kGroupTiles : n_tiles;
     for (int col = threadIdx.x; col < width; col += blockDim.x) {
         double acc = 0.0;
-        for (uint64_t t = lo; t < hi; ++t) acc += tile_sums[t * width + col];
-        group_sums[g * width + col] = acc;
+        for (uint64_t t = lo; t < hi; ++t) acc += rows[t * width + col];
+        out_row[col] = acc;
     }
 }
 
-__global__ void reduce_final_kernel(const double *group_sums, uint64_t n_groups, int n_contracts,
-                                    double n_paths, int gamma_nan, double *out)
+// Sum n_groups group rows in order and write mean / SE per estimator.
+__device__ __forceinline__ void finish_groups(const double *group_sums, uint64_t n_groups,
+                                              int n_contracts, double n_paths, int gamma_nan,
+                                              double *out)
 {
     __shared__ double tot[12 * kMaxC];
     const int width = 12 * n_contracts;
@@ -797,6 +797,135 @@ __global__ void reduce_final_kernel(const double *group_sums, uint64_t n_groups,
         out[c * 12 + j] = m;
         out[c * 12 + 6 + j] = se;
     }
+}
+
+__global__ void reduce_groups_kernel(const double *tile_sums, uint64_t n_tiles, int width,
+                                     double *group_sums)
+{
+    const uint64_t g = blockIdx.x;
+    const uint64_t lo = g * kGroupTiles;
+    const uint64_t hi = lo + kGroupTiles < n_tiles ? lo + kGroupTiles : n_tiles;
+    sum_rows(tile_sums, lo, hi, width, group_sums + g * width);
+}
+
+__global__ void reduce_final_kernel(const double *group_sums, uint64_t n_groups, int n_contracts,
+                                    double n_paths, int gamma_nan, double *out)
+{
+    finish_groups(group_sums, n_groups, n_contracts, n_paths, gamma_nan, out);
+}
+
+// ---------------------------------------------------------------------------
+// Batched persistent launch: many contracts, each with its own parameters,
+// path count, step count and seed, in one launch.  Work items are
+// (contract, 64-path tile) pairs handed out through an atomic counter,
+// contracts with the most steps first; each contract's tile rows and their
+// reduction (sum_rows / finish_groups) are those of its own launch, so every
+// result equals the contract's own launch bit for bit.  A device status word
+// lets a caller stop the launch between work items: 0 = run, 1 = cancel
+// requested, 2 = the kernel saw the request and took no further work.
+// ---------------------------------------------------------------------------
+struct BatchItemDev {
+    Coef<float> k;
+    ContractSet<float> cs;        // one contract
+    PhiloxKey key;
+    uint64_t n_paths;
+    uint64_t n_tiles;
+    uint64_t row_begin;           // first tile row of this contract
+    uint64_t group_begin;         // first group row of this contract
+    uint32_t N;
+    int32_t mon;
+    int32_t gamma_nan;
+    int32_t pad;
+};
+
+struct BatchLaunch {
+    const BatchItemDev *items;    // caller order
+    const uint64_t *work_begin;   // [n_items] first work index of the p-th contract in work order
+    const uint32_t *work_item;    // [n_items] contract of the p-th position in work order
+    const uint64_t *group_begin;  // [n_items] (caller order) first group row, for the reductions
+    uint32_t n_items;
+    uint64_t total_work;
+    unsigned long long *counter;
+    int32_t *status;
+    double *rows;
+};
+
+template <int TRUNC>
+__global__ void __launch_bounds__(kPathBlock) heston_batch_kernel(BatchLaunch a)
+{
+    const int lane = threadIdx.x & 31;
+    bool saw_cancel = false;
+    while (true) {
+        unsigned long long g = ~0ull;
+        if (lane == 0) {
+            const int32_t st = a.status ? *(volatile int32_t *)a.status : 0;
+            if (st != 0) saw_cancel = true;
+            else g = atomicAdd(a.counter, 1ull);
+        }
+        g = __shfl_sync(0xffffffffu, g, 0);
+        if (g >= a.total_work) break;
+        uint32_t lo = 0, hi = a.n_items;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (a.work_begin[mid] <= g) lo = mid; else hi = mid;
+        }
+        const BatchItemDev &it = a.items[a.work_item[lo]];
+        const uint64_t t = g - a.work_begin[lo];
+        const Coef<float> k = it.k;
+        const PhiloxKey key = it.key;
+        PathState<float> s[2];
+        uint32_t plo[2], phi[2];
+        bool keep[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const uint64_t local = t * kTile + (uint64_t)lane + 32u * (uint64_t)q;
+            keep[q] = local < it.n_paths;
+            plo[q] = (uint32_t)local;
+            phi[q] = (uint32_t)(local >> 32);
+        }
+        if (it.mon == MON_NONE)       simulate<float, TRUNC, MON_NONE, 2>(s, plo, phi, k, it.cs, key, it.N);
+        else if (it.mon == MON_EVERY) simulate<float, TRUNC, MON_EVERY, 2>(s, plo, phi, k, it.cs, key, it.N);
+        else                          simulate<float, TRUNC, MON_STRIDE, 2>(s, plo, phi, k, it.cs, key, it.N);
+        float e0[6], e1[6];
+        estimators(s[0], it.cs, 0, exp_r(s[0].X), e0);
+        estimators(s[1], it.cs, 0, exp_r(s[1].X), e1);
+        double *row = a.rows + (it.row_begin + t) * 12u;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+            const float x0 = keep[0] ? e0[j] : 0.0f, x1 = keep[1] ? e1[j] : 0.0f;
+            const float sx = warp_sum(x0 + x1);
+            const float sxx = warp_sum(x0 * x0 + x1 * x1);
+            if (lane == j) row[j] = (double)sx;
+            if (lane == 6 + j) row[6 + j] = (double)sxx;
+        }
+    }
+    if (saw_cancel) atomicCAS(a.status, 1, 2);
+}
+
+// One block per group row of the whole batch: the contract is found from
+// the flat group index.
+__global__ void batch_reduce_groups_kernel(const BatchItemDev *items, const uint64_t *group_begin,
+                                           uint32_t n_items, const double *rows, double *groups)
+{
+    const uint64_t g = blockIdx.x;
+    uint32_t lo = 0, hi = n_items;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (group_begin[mid] <= g) lo = mid; else hi = mid;
+    }
+    const BatchItemDev &it = items[lo];
+    const uint64_t j = g - it.group_begin;
+    const uint64_t t0 = j * kGroupTiles;
+    const uint64_t t1 = t0 + kGroupTiles < it.n_tiles ? t0 + kGroupTiles : it.n_tiles;
+    sum_rows(rows + it.row_begin * 12u, t0, t1, 12, groups + g * 12u);
+}
+
+__global__ void batch_reduce_final_kernel(const BatchItemDev *items, const double *groups, double *out)
+{
+    const BatchItemDev &it = items[blockIdx.x];
+    const uint64_t ng = (it.n_tiles + kGroupTiles - 1) / kGroupTiles;
+    finish_groups(groups + it.group_begin * 12u, ng, 1, (double)it.n_paths, it.gamma_nan,
+                  out + (uint64_t)blockIdx.x * 12u);
 }
 
 // ---------------------------------------------------------------------------
@@ -1048,8 +1177,11 @@ int enqueue(const Prepared &pp, uint64_t n_paths, uint64_t seed, void *ws, size_
     return HESTON_OK;
 }
 
-void fill_results(const double *h, uint32_t nc, uint64_t n_paths, int status, heston_result *out)
+// Fill host results; returns the largest per-contract status (a warning
+// for non-finite Vega / Theta outranks the Gamma one).
+int fill_results(const double *h, uint32_t nc, uint64_t n_paths, int status, heston_result *out)
 {
+    int worst = status;
     for (uint32_t c = 0; c < nc; ++c) {
         heston_result &r = out[c];
         r.price = h[c * 12 + 0]; r.delta = h[c * 12 + 1]; r.gamma = h[c * 12 + 2];
@@ -1057,8 +1189,13 @@ void fill_results(const double *h, uint32_t nc, uint64_t n_paths, int status, he
         for (int j = 0; j < 6; ++j) r.se[j] = h[c * 12 + 6 + j];
         r.n_paths = n_paths;
         r.status = status;
+        if (!std::isfinite(r.vega) || !std::isfinite(r.theta) || !std::isfinite(r.se[3]) ||
+            !std::isfinite(r.se[5]))
+            r.status = HESTON_WARN_TANGENT_UNSTABLE;
+        if (r.status > worst) worst = r.status;
         r.reserved = 0;
     }
+    return worst;
 }
 
 
@@ -1385,6 +1522,172 @@ int build_qmc_tables(uint32_t N, void *d_tables, size_t bytes)
     return HESTON_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// Host: batched launch
+// ---------------------------------------------------------------------------
+struct BatchDescLayout {
+    size_t off_items, off_work_begin, off_work_item, off_group_begin, total;
+};
+
+BatchDescLayout batch_desc_layout(uint32_t n)
+{
+    BatchDescLayout L;
+    L.off_items = 0;
+    L.off_work_begin = align256((size_t)n * sizeof(BatchItemDev));
+    L.off_work_item = L.off_work_begin + align256((size_t)n * sizeof(uint64_t));
+    L.off_group_begin = L.off_work_item + align256((size_t)n * sizeof(uint32_t));
+    L.total = L.off_group_begin + align256((size_t)n * sizeof(uint64_t));
+    return L;
+}
+
+// Workspace: counter | tile rows | group rows.
+struct BatchWsLayout {
+    size_t off_counter, off_rows, off_groups, total;
+};
+
+BatchWsLayout batch_ws_layout(uint64_t tiles, uint64_t groups)
+{
+    BatchWsLayout L;
+    L.off_counter = 0;
+    L.off_rows = 256;
+    L.off_groups = L.off_rows + align256(tiles * 12u * sizeof(double));
+    L.total = L.off_groups + align256(groups * 12u * sizeof(double));
+    return L;
+}
+
+int batch_prepare_items(const heston_batch_item *items, uint32_t n, const heston_options *opts,
+                        std::vector<BatchItemDev> *dev, heston_batch_plan *plan)
+{
+    if (!items || n == 0 || !plan) return HESTON_ERR_INVALID_ARG;
+    heston_options o;
+    if (opts) o = *opts; else { std::memset(&o, 0, sizeof(o)); o.device = -1; }
+    if (o.prec != HESTON_FP32 || o.rng != HESTON_RNG_PHILOX) return HESTON_ERR_UNSUPPORTED;
+    uint64_t tiles = 0, groups = 0, ps = 0;
+    if (dev) dev->resize(n);
+    for (uint32_t i = 0; i < n; ++i) {
+        if (items[i].reserved != 0) return HESTON_ERR_INVALID_ARG;
+        Prepared pp;
+        const int rc = validate_and_prepare(&items[i].params, &items[i].contract, 1, items[i].n_paths,
+                                            items[i].n_steps, &o, pp);
+        if (rc < 0) return rc;
+        const uint64_t nt = tiles_for(items[i].n_paths);
+        if (dev) {
+            BatchItemDev &d = (*dev)[i];
+            std::memset(&d, 0, sizeof(d));
+            d.k = pp.kf;
+            d.cs = pp.csf;
+            d.key = key_of(items[i].rng_seed);
+            d.n_paths = items[i].n_paths;
+            d.n_tiles = nt;
+            d.row_begin = tiles;
+            d.group_begin = groups;
+            d.N = items[i].n_steps;
+            d.mon = mon_mode(pp.cs);
+            d.gamma_nan = pp.gamma_nan ? 1 : 0;
+        }
+        tiles += nt;
+        groups += groups_for(nt);
+        ps += items[i].n_paths * (uint64_t)items[i].n_steps;
+    }
+    plan->total_tiles = tiles;
+    plan->total_groups = groups;
+    plan->total_path_steps = ps;
+    plan->n_items = n;
+    plan->trunc = o.trunc;
+    plan->descriptor_bytes = batch_desc_layout(n).total;
+    plan->workspace_bytes = batch_ws_layout(tiles, groups).total;
+    return HESTON_OK;
+}
+
+int batch_prepare(const heston_batch_item *items, const heston_options *opts,
+                  const heston_batch_plan *plan, void *d_desc)
+{
+    if (!plan || !d_desc || ((uintptr_t)d_desc & 255u)) return HESTON_ERR_INVALID_ARG;
+    const uint32_t n = plan->n_items;
+    std::vector<BatchItemDev> dev;
+    heston_batch_plan check;
+    int rc = batch_prepare_items(items, n, opts, &dev, &check);
+    if (rc < 0) return rc;
+    if (check.total_tiles != plan->total_tiles || check.total_groups != plan->total_groups)
+        return HESTON_ERR_INVALID_ARG;
+    // work order: most steps first (ties: caller order)
+    std::vector<uint32_t> order(n);
+    for (uint32_t i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](uint32_t x, uint32_t y) { return dev[x].N > dev[y].N; });
+    std::vector<uint64_t> wb(n), gb(n);
+    uint64_t acc = 0;
+    for (uint32_t p = 0; p < n; ++p) { wb[p] = acc; acc += dev[order[p]].n_tiles; }
+    for (uint32_t i = 0; i < n; ++i) gb[i] = dev[i].group_begin;
+    const BatchDescLayout L = batch_desc_layout(n);
+    std::vector<unsigned char> h(L.total, 0);
+    std::memcpy(h.data() + L.off_items, dev.data(), n * sizeof(BatchItemDev));
+    std::memcpy(h.data() + L.off_work_begin, wb.data(), n * sizeof(uint64_t));
+    std::memcpy(h.data() + L.off_work_item, order.data(), n * sizeof(uint32_t));
+    std::memcpy(h.data() + L.off_group_begin, gb.data(), n * sizeof(uint64_t));
+    if (cudaMemcpy(d_desc, h.data(), L.total, cudaMemcpyHostToDevice) != cudaSuccess) return HESTON_ERR_CUDA;
+    return HESTON_OK;
+}
+
+template <int TRUNC>
+cudaError_t launch_batch_t(const BatchLaunch &a, const heston_options &o, cudaStream_t st)
+{
+    auto kern = heston_batch_kernel<TRUNC>;
+    int dev = 0, n_sm = 0, per_sm = 0;
+    const int block = o.block_threads ? (int)o.block_threads : kPathBlock;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    const uint64_t warps_per_cta = (uint64_t)block / 32;
+    uint64_t grid = o.grid_ctas ? o.grid_ctas
+                                : std::min<uint64_t>((a.total_work + warps_per_cta - 1) / warps_per_cta,
+                                                     (uint64_t)n_sm * per_sm);
+    if (grid < 1) grid = 1;
+    kern<<<(unsigned)grid, block, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+int batch_launch(const heston_batch_plan *plan, const void *d_desc, const heston_options *opts,
+                 void *ws, double *d_out, int32_t *d_status)
+{
+    if (!plan || !d_desc || !ws || !d_out || ((uintptr_t)d_desc & 255u) || ((uintptr_t)ws & 255u))
+        return HESTON_ERR_INVALID_ARG;
+    heston_options o;
+    if (opts) o = *opts; else { std::memset(&o, 0, sizeof(o)); o.device = -1; }
+    if (o.block_threads != 0 && (o.block_threads % 32 != 0 || o.block_threads > kPathBlock))
+        return HESTON_ERR_INVALID_ARG;
+    DeviceGuard g(o.device);
+    if (g.err != cudaSuccess) return HESTON_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)o.cuda_stream;
+    const uint32_t n = plan->n_items;
+    const BatchDescLayout L = batch_desc_layout(n);
+    const BatchWsLayout W = batch_ws_layout(plan->total_tiles, plan->total_groups);
+    const char *d = (const char *)d_desc;
+    char *w = (char *)ws;
+    BatchLaunch a;
+    a.items = (const BatchItemDev *)(d + L.off_items);
+    a.work_begin = (const uint64_t *)(d + L.off_work_begin);
+    a.work_item = (const uint32_t *)(d + L.off_work_item);
+    a.group_begin = (const uint64_t *)(d + L.off_group_begin);
+    a.n_items = n;
+    a.total_work = plan->total_tiles;
+    a.counter = (unsigned long long *)(w + W.off_counter);
+    a.status = d_status;
+    a.rows = (double *)(w + W.off_rows);
+    if (cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), st) != cudaSuccess) return HESTON_ERR_CUDA;
+    const cudaError_t e = plan->trunc == HESTON_TRUNC_FULL ? launch_batch_t<0>(a, o, st) : launch_batch_t<1>(a, o, st);
+    if (e != cudaSuccess) return HESTON_ERR_CUDA;
+    double *groups = (double *)(w + W.off_groups);
+    batch_reduce_groups_kernel<<<(unsigned)plan->total_groups, 64, 0, st>>>(a.items, a.group_begin, n,
+                                                                            a.rows, groups);
+    if (cudaGetLastError() != cudaSuccess) return HESTON_ERR_CUDA;
+    batch_reduce_final_kernel<<<n, 64, 0, st>>>(a.items, groups, d_out);
+    return cudaGetLastError() == cudaSuccess ? HESTON_OK : HESTON_ERR_CUDA;
+}
+
 }  // namespace
 
 // Static device scratch of heston_mc_launch_noalloc (see include/heston_mc.h):
@@ -1447,8 +1750,7 @@ int qmc_price_sync(const Prepared &pp, uint64_t n_paths, uint64_t seed, heston_r
     if (cudaStreamSynchronize(st) != cudaSuccess) e = HESTON_ERR_CUDA;
     if (e < 0) return e;
     const int status = pp.gamma_nan ? HESTON_WARN_GAMMA_UNDEFINED : HESTON_OK;
-    fill_results(h, (uint32_t)pp.cs.n, n_paths, status, out);
-    return status;
+    return fill_results(h, (uint32_t)pp.cs.n, n_paths, status, out);
 }
 }  // namespace
 
@@ -1462,6 +1764,7 @@ const char *heston_status_string(int status)
     switch (status) {
     case HESTON_OK: return "ok";
     case HESTON_WARN_GAMMA_UNDEFINED: return "gamma undefined (|rho| == 1 or v0 == 0); set to NaN";
+    case HESTON_WARN_TANGENT_UNSTABLE: return "vega / theta not finite: pathwise tangents unstable near V = 0";
     case HESTON_ERR_INVALID_ARG: return "invalid argument";
     case HESTON_ERR_CUDA: return "CUDA runtime error";
     case HESTON_ERR_NOMEM: return "device allocation failed";
@@ -1562,8 +1865,7 @@ int heston_mc_price_greeks_ex(const heston_params *params, const heston_contract
         return e;
     }
     const int status = pp.gamma_nan ? HESTON_WARN_GAMMA_UNDEFINED : HESTON_OK;
-    fill_results(h, n_contracts, n_paths, status, out);
-    return status;
+    return fill_results(h, n_contracts, n_paths, status, out);
 }
 
 int heston_mc_price_greeks(const heston_params *params, const heston_contract *contract,
@@ -1698,6 +2000,64 @@ int heston_rng_debug(uint64_t rng_seed, const uint64_t *paths, const uint32_t *s
         e = HESTON_ERR_CUDA;
     cudaFree(buf);
     return e;
+}
+
+int heston_batch_plan_make(const heston_batch_item *items, uint32_t n_items,
+                           const heston_options *opts, heston_batch_plan *plan)
+{
+    return batch_prepare_items(items, n_items, opts, nullptr, plan);
+}
+
+int heston_batch_prepare(const heston_batch_item *items, const heston_options *opts,
+                         const heston_batch_plan *plan, void *d_desc)
+{
+    if (!plan) return HESTON_ERR_INVALID_ARG;
+    DeviceGuard g(opts ? opts->device : -1);
+    if (g.err != cudaSuccess) return HESTON_ERR_CUDA;
+    return batch_prepare(items, opts, plan, d_desc);
+}
+
+int heston_mc_launch_batch(const heston_batch_plan *plan, const void *d_desc,
+                           const heston_options *opts, void *d_workspace, double *d_out,
+                           int32_t *d_status)
+{
+    return batch_launch(plan, d_desc, opts, d_workspace, d_out, d_status);
+}
+
+int heston_mc_price_greeks_batch(const heston_batch_item *items, uint32_t n_items,
+                                 const heston_options *opts, heston_result *out)
+{
+    if (!out) return HESTON_ERR_INVALID_ARG;
+    heston_batch_plan plan;
+    int rc = batch_prepare_items(items, n_items, opts, nullptr, &plan);
+    if (rc < 0) return rc;
+    DeviceGuard g(opts ? opts->device : -1);
+    if (g.err != cudaSuccess) return HESTON_ERR_CUDA;
+    cudaStream_t st = opts ? (cudaStream_t)opts->cuda_stream : nullptr;
+    const size_t ob = align256((size_t)n_items * 12u * sizeof(double));
+    char *buf = nullptr;
+    if (cudaMalloc((void **)&buf, plan.descriptor_bytes + plan.workspace_bytes + ob) != cudaSuccess) {
+        cudaGetLastError();
+        return HESTON_ERR_NOMEM;
+    }
+    double *d_out = (double *)(buf + plan.descriptor_bytes + plan.workspace_bytes);
+    int e = batch_prepare(items, opts, &plan, buf);
+    if (e == HESTON_OK) e = batch_launch(&plan, buf, opts, buf + plan.descriptor_bytes, d_out, nullptr);
+    std::vector<double> h((size_t)n_items * 12u);
+    if (e == HESTON_OK && cudaMemcpyAsync(h.data(), d_out, h.size() * sizeof(double),
+                                          cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        e = HESTON_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) e = HESTON_ERR_CUDA;
+    cudaFree(buf);
+    if (e < 0) return e;
+    int worst = HESTON_OK;
+    for (uint32_t i = 0; i < n_items; ++i) {
+        const bool gn = std::fabs(items[i].params.rho) == 1.0 || items[i].params.v0 == 0.0;
+        const int status = fill_results(h.data() + (size_t)i * 12u, 1, items[i].n_paths,
+                                        gn ? HESTON_WARN_GAMMA_UNDEFINED : HESTON_OK, out + i);
+        if (status > worst) worst = status;
+    }
+    return worst;
 }
 
 int heston_sobol_directions(uint32_t n_dims, uint32_t *h_out)

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libhestonmc.so")
 
 HESTON_OK = 0
 HESTON_WARN_GAMMA_UNDEFINED = 1
+HESTON_WARN_TANGENT_UNSTABLE = 2
 HESTON_ERR_INVALID_ARG = -1
 HESTON_ERR_CUDA = -2
 HESTON_ERR_NOMEM = -3
@@ -62,6 +63,19 @@ class heston_result(ctypes.Structure):
         ("reserved", ctypes.c_int32)]
 
 
+class heston_batch_item(ctypes.Structure):
+    _fields_ = [("params", heston_params), ("contract", heston_contract), ("n_paths", ctypes.c_uint64),
+                ("n_steps", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("rng_seed", ctypes.c_uint64)]
+
+
+class heston_batch_plan(ctypes.Structure):
+    _fields_ = [("total_tiles", ctypes.c_uint64), ("total_groups", ctypes.c_uint64),
+                ("total_path_steps", ctypes.c_uint64), ("n_items", ctypes.c_uint32),
+                ("trunc", ctypes.c_int32), ("descriptor_bytes", ctypes.c_size_t),
+                ("workspace_bytes", ctypes.c_size_t)]
+
+
 class HestonError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{msg} (status {status})")
@@ -101,6 +115,13 @@ def load():
                                    P(ctypes.c_double)], i32),
         "heston_rng_debug": ([u64, P(u64), P(u32), u32, i32, P(u32), P(ctypes.c_double)], i32),
         "heston_status_string": ([ctypes.c_int], ctypes.c_char_p),
+        "heston_batch_plan_make": ([P(heston_batch_item), u32, P(heston_options),
+                                    P(heston_batch_plan)], i32),
+        "heston_batch_prepare": ([P(heston_batch_item), P(heston_options), P(heston_batch_plan), vp],
+                                 i32),
+        "heston_mc_launch_batch": ([P(heston_batch_plan), vp, P(heston_options), vp, vp, vp], i32),
+        "heston_mc_price_greeks_batch": ([P(heston_batch_item), u32, P(heston_options),
+                                          P(heston_result)], i32),
         "heston_sobol_directions": ([u32, P(u32)], i32),
         "heston_qmc_tables_bytes": ([u32, P(sz)], i32),
         "heston_qmc_build_tables": ([u32, vp, sz, i32], i32),
@@ -302,3 +323,42 @@ def heston_qmc_debug_paths(params, contracts, n_steps, rng_seed, options, replic
                                          points.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
                                          n, rec.ctypes.data_as(D), est.ctypes.data_as(D)))
     return rec, est
+
+
+def make_batch_item(params: heston_params, contract: heston_contract, n_paths: int, n_steps: int,
+                    rng_seed: int) -> heston_batch_item:
+    return heston_batch_item(params, contract, n_paths, n_steps, 0, rng_seed)
+
+
+def _items_array(items):
+    arr = (heston_batch_item * len(items))()
+    for i, it in enumerate(items):
+        arr[i] = it
+    return arr
+
+
+def heston_batch_plan_make(items, options=None) -> heston_batch_plan:
+    plan = heston_batch_plan()
+    arr = _items_array(items)
+    opt = ctypes.byref(options) if options is not None else None
+    _check(load().heston_batch_plan_make(arr, len(items), opt, ctypes.byref(plan)))
+    return plan
+
+
+def heston_batch_prepare(items, options, plan, desc) -> int:
+    arr = _items_array(items)
+    return _check(load().heston_batch_prepare(arr, ctypes.byref(options), ctypes.byref(plan),
+                                              _ptr(desc)))
+
+
+def heston_mc_launch_batch(plan, desc, options, workspace, out, status=None) -> int:
+    return _check(load().heston_mc_launch_batch(ctypes.byref(plan), _ptr(desc), ctypes.byref(options),
+                                                _ptr(workspace), _ptr(out), _ptr(status) or None))
+
+
+def heston_mc_price_greeks_batch(items, options=None):
+    arr = _items_array(items)
+    out = (heston_result * len(items))()
+    opt = ctypes.byref(options) if options is not None else None
+    _check(load().heston_mc_price_greeks_batch(arr, len(items), opt, out))
+    return list(out)
