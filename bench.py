@@ -392,6 +392,42 @@ def run_gpu(args):
                                     "tuned_candidates": len(tune_ms)},
                    "graph": "memset + persistent kernel + 2 reductions captured, replayed"}
 
+    # adjoint gradient: 252-step Asian call, 2^20 paths, d price / d (S0, v0, kappa, theta, xi, rho, r)
+    adjoint = None
+    if not args.no_adjoint and world == 1:
+        an, aN = 1 << 20, 252
+        ac = nv.make_contract(1, 100.0, 1.0)
+        aws_bytes = nv.heston_adjoint_workspace_bytes(an, aN)
+        aws = torch.empty(aws_bytes // 8 + 32, dtype=torch.float64, device=dev)
+        aprice = torch.empty(2, dtype=torch.float64, device=dev)
+        agrad = torch.empty(14, dtype=torch.float64, device=dev)
+        aopts = nv.make_options(prec=nv.HESTON_FP32, stream=stream, device=local)
+        for _ in range(2):
+            nv.heston_mc_adjoint_forward(params, ac, an, aN, w.seed, aopts, aws, aws_bytes, aprice)
+            nv.heston_mc_adjoint_backward(params, ac, an, aN, w.seed, aopts, aws, aws_bytes, agrad)
+        barrier()
+        a_steps = 5
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        fwd, bwd = [], []
+        clocks.mark(True)
+        for _ in range(a_steps):
+            ev[0].record(stream)
+            nv.heston_mc_adjoint_forward(params, ac, an, aN, w.seed, aopts, aws, aws_bytes, aprice)
+            ev[1].record(stream)
+            nv.heston_mc_adjoint_backward(params, ac, an, aN, w.seed, aopts, aws, aws_bytes, agrad)
+            ev[2].record(stream)
+            ev[2].synchronize()
+            fwd.append(ev[0].elapsed_time(ev[1]))
+            bwd.append(ev[1].elapsed_time(ev[2]))
+        clocks.mark(False)
+        gv = agrad.cpu().numpy()
+        adjoint = {"workload": "Asian call K=100, 252 dates/steps, 2^20 paths, FP32 path / FP64 sums",
+                   "forward_ms": statistics.mean(fwd), "backward_ms": statistics.mean(bwd),
+                   "checkpoint_every_steps": 16,
+                   "price": float(aprice[0]), "gradient": dict(zip(
+                       ("S0", "v0", "kappa", "theta", "xi", "rho", "r"), gv[:7].tolist())),
+                   "gradient_se": gv[7:].tolist()}
+
     # end to end through the synchronous host API (host structs in, results out)
     res_arr = (nv.heston_result * nc)()
     carr = (nv.heston_contract * nc)(*contracts)
@@ -458,6 +494,8 @@ def run_gpu(args):
             line["qmc_variant"] = qmc
         if batched is not None:
             line["batched_variant"] = batched
+        if adjoint is not None:
+            line["adjoint_variant"] = adjoint
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
         print(json.dumps(line), flush=True)
@@ -476,6 +514,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-qmc", action="store_true", help="skip the quasi-Monte Carlo variant")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 1024-contract form")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint gradient")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--n-paths", type=int, default=0,
                     help="paths per rank (default: the workload's 2^22); small cases for ncu")

@@ -353,6 +353,34 @@ int heston_mc_launch_batch(const heston_batch_plan *plan, const void *d_desc,
 int heston_mc_price_greeks_batch(const heston_batch_item *items, uint32_t n_items,
                                  const heston_options *opts, heston_result *out);
 
+/* ---- adjoint (reverse-mode pathwise) parameter gradient -------------------- */
+
+/* Gradient of the discounted price of one contract with respect to
+ * (S0, v0, kappa, theta, xi, rho, r): the pathwise method (Sec. 2, the
+ * chain rule through the path, Eq. pw_est) applied in reverse mode to the
+ * Milstein recursion with full truncation.  FP32 paths, FP64 sums, Philox
+ * normals, n_steps <= 1024; other options return HESTON_ERR_UNSUPPORTED.
+ * The forward call prices the contract and stores, per path, (X, V) every
+ * C = ceil(sqrt(n_steps)) steps and the payoff slope; the backward call
+ * rebuilds each C-step segment from its checkpoint (normals recomputed from
+ * their Philox counters) and runs the adjoint sweep.  Both are asynchronous
+ * on opts->cuda_stream, allocate nothing, and must use the same workspace,
+ * inputs and seed, the backward after the forward.
+ *   d_workspace: device, 256-byte aligned, >= heston_adjoint_workspace_bytes.
+ *   d_price: device, 2 doubles (price, SE).
+ *   d_grad:  device, 14 doubles (the 7 derivatives, then their SEs). */
+int heston_adjoint_workspace_bytes(uint64_t n_paths, uint32_t n_steps, size_t *bytes);
+
+int heston_mc_adjoint_forward(const heston_params *params, const heston_contract *contract,
+                              uint64_t n_paths, uint32_t n_steps, uint64_t rng_seed,
+                              const heston_options *opts, void *d_workspace, size_t workspace_bytes,
+                              double *d_price);
+
+int heston_mc_adjoint_backward(const heston_params *params, const heston_contract *contract,
+                               uint64_t n_paths, uint32_t n_steps, uint64_t rng_seed,
+                               const heston_options *opts, void *d_workspace, size_t workspace_bytes,
+                               double *d_grad);
+
 /* ---- test support --------------------------------------------------------- */
 
 /* Per-path dump for `count` global path indices (host array `paths`):

@@ -91,6 +91,10 @@ def _load():
         lib.orc_paths_from_normals.argtypes = [P(_Params), P(_Contract), u32, u32, i32, u64,
                                                P(d), P(d), P(d), P(d)]
         lib.orc_paths_from_normals.restype = i32
+        lib.orc_mc_gradient.argtypes = [P(_Params), P(_Contract), u64, u32, u64, P(d), P(d)]
+        lib.orc_mc_gradient.restype = i32
+        lib.orc_debug_gradients.argtypes = [P(_Params), P(_Contract), P(u64), u64, u32, u64, P(d)]
+        lib.orc_debug_gradients.restype = i32
         lib.orc_max_threads.restype = i32
         _lib = lib
     return _lib
@@ -244,6 +248,33 @@ def paths_from_normals(params: Params, contracts, za, zb, trunc=TRUNC_FULL):
                                     _dptr(zb), _dptr(rec), _dptr(est))
     _check_rc(rc)
     return rec, est
+
+
+PARAM_NAMES = ("S0", "v0", "kappa", "theta", "xi", "rho", "r")
+
+
+def mc_gradient(params: Params, contract: Contract, n_paths, n_steps, seed):
+    """Price and d price / d (S0, v0, kappa, theta, xi, rho, r) with SEs
+    (forward-mode tangents, full truncation): two arrays of 8."""
+    lib = _load()
+    cs = _contracts([contract])
+    mean = np.zeros(8)
+    se = np.zeros(8)
+    p = params._c()
+    _check_rc(lib.orc_mc_gradient(ctypes.byref(p), cs, n_paths, n_steps, seed, _dptr(mean), _dptr(se)))
+    return mean, se
+
+
+def debug_gradients(params: Params, contract: Contract, paths, n_steps, seed):
+    """Per-path (payoff, 7 derivatives): (count, 8)."""
+    lib = _load()
+    paths = np.ascontiguousarray(np.asarray(paths, dtype=np.uint64))
+    out = np.zeros((len(paths), 8))
+    p = params._c()
+    _check_rc(lib.orc_debug_gradients(ctypes.byref(p), _contracts([contract]),
+                                      paths.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                      len(paths), n_steps, seed, _dptr(out)))
+    return out
 
 
 def max_threads() -> int:

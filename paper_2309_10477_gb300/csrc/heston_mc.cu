@@ -134,6 +134,7 @@ struct Coef {
     R kdt, kth_dt, kth_ddt, kappa_ddt;
     R xi, c4, c4T;                // c4 = xi^2 dt / 4, c4T = xi^2 / (4N)
     R rho, sq;                    // sq = sqrt(1 - rho^2)
+    R kappa, theta;               // for the adjoint
 };
 
 // Contracts priced on the shared paths (all with the same T and Asian M),
@@ -928,6 +929,195 @@ __global__ void batch_reduce_final_kernel(const BatchItemDev *items, const doubl
                   out + (uint64_t)blockIdx.x * 12u);
 }
 
+
+// ---------------------------------------------------------------------------
+// Adjoint (reverse-mode pathwise) gradient of the price with respect to
+// (S0, v0, kappa, theta, xi, rho, r), full truncation, FP32 paths, FP64 sums.
+// The forward kernel prices and stores, per path, (X, V) every C = ceil(sqrt N)
+// steps plus the payoff seed; the backward kernel rebuilds each C-step segment
+// from its checkpoint (normals recomputed from the Philox counters) and sweeps
+// the adjoints of the Milstein step (Sec. 2.4.2) in reverse:
+//   X' = X + (r - V+/2) dt + u Za,   u = sqrt(V+ dt),   Z2 = rho Za + s Zb,
+//   V' = V + kappa (theta - V+) dt + xi u Z2 + xi^2 dt (Z2^2 - 1) 1{V>0} / 4,
+// with P = e^{-rT} phi(A), A = S0 e^{X_N} or (S0/M) sum_i e^{X(t_i)}.
+// ---------------------------------------------------------------------------
+constexpr int kAdjMaxSeg = 32;             // segment length C <= 32: n_steps <= 1024
+
+struct AdjLaunch {
+    PhiloxKey key;
+    uint64_t n_paths, n_tiles;
+    uint32_t N, C, n_seg;                   // steps, segment length, segments
+    float2 *ckpt;                           // [n_seg][n_paths] (X, V) at each segment start
+    float2 *seed;                           // [n_paths] (payoff, D phi'(A) / M or D phi'(S_T))
+    double *rows;                           // tile rows
+};
+
+// Normals of step k of a path (words by parity, as in simulate()).
+__device__ __forceinline__ void step_normals(PhiloxKey key, uint32_t plo, uint32_t phi, uint32_t k,
+                                             float &za, float &zb)
+{
+    const uint4 w = philox4x32_10(make_uint4(k >> 1, plo, phi, 0u), key);
+    if (k & 1u) box_muller(w.z, w.w, za, zb);
+    else        box_muller(w.x, w.y, za, zb);
+}
+
+// One plain Milstein step (no tangents), full truncation: the forward of the adjoint.
+__device__ __forceinline__ void plain_step(float &X, float &V, float za, float zb, const Coef<float> &k)
+{
+    const float Z2 = fmaf(k.rho, za, k.sq * zb);
+    const bool pos = V > 0.0f;
+    const float Vp = fmaxf(V, 0.0f);
+    const float u = sqrt_approx(Vp * k.dt);
+    X = fmaf(u, za, fmaf(fmaf(-0.5f, Vp, k.r), k.dt, X));
+    const float z2m1 = fmaf(Z2, Z2, -1.0f);
+    V = fmaf(pos ? k.c4 : 0.0f, z2m1, fmaf(k.xi * Z2, u, fmaf(-k.kdt, Vp, V + k.kth_dt)));
+}
+
+template <int MON>
+__global__ void __launch_bounds__(kPathBlock) heston_adj_fwd_kernel(Coef<float> k, ContractSet<float> cs,
+                                                                    AdjLaunch a)
+{
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t tile = warp; tile < a.n_tiles; tile += n_warps) {
+        float x[2];
+#pragma unroll 1
+        for (int q = 0; q < 2; ++q) {
+            const uint64_t path = tile * kTile + (uint64_t)lane + 32u * (uint64_t)q;
+            const bool keep = path < a.n_paths;
+            const uint32_t plo = (uint32_t)path, phi = (uint32_t)(path >> 32);
+            float X = 0.0f, V = k.v0, sA = 0.0f;
+            for (uint32_t kk = 0; kk < a.N; ++kk) {
+                if (keep && kk % a.C == 0) a.ckpt[(uint64_t)(kk / a.C) * a.n_paths + path] = make_float2(X, V);
+                float za, zb;
+                step_normals(a.key, plo, phi, kk, za, zb);
+                plain_step(X, V, za, zb, k);
+                if (MON != MON_NONE && (kk + 1) % cs.stride == 0) sA += exp_r(X);
+            }
+            const float A = MON == MON_NONE ? cs.S0 * exp_r(X) : cs.S0_over_M * sA;
+            const float K = cs.K[0];
+            float pay, slope;
+            if (!cs.is_put[0]) { slope = A > K ? 1.0f : 0.0f; pay = A > K ? A - K : 0.0f; }
+            else               { slope = A < K ? -1.0f : 0.0f; pay = A < K ? K - A : 0.0f; }
+            const float scale = MON == MON_NONE ? 1.0f : 1.0f / (float)cs.M;
+            if (keep) a.seed[path] = make_float2(cs.D * pay, cs.D * slope * scale);
+            x[q] = keep ? cs.D * pay : 0.0f;
+        }
+        const float sx = warp_sum(x[0] + x[1]);
+        const float sxx = warp_sum(x[0] * x[0] + x[1] * x[1]);
+        if (lane == 0) { a.rows[tile * 2] = (double)sx; a.rows[tile * 2 + 1] = (double)sxx; }
+    }
+}
+
+template <int MON>
+__global__ void __launch_bounds__(kPathBlock) heston_adj_bwd_kernel(Coef<float> k, ContractSet<float> cs,
+                                                                    AdjLaunch a, float T)
+{
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const float inv_sq = 1.0f / k.sq;
+    for (uint64_t tile = warp; tile < a.n_tiles; tile += n_warps) {
+        float g[2][7];
+#pragma unroll 1
+        for (int q = 0; q < 2; ++q) {
+            const uint64_t path = tile * kTile + (uint64_t)lane + 32u * (uint64_t)q;
+            const bool keep = path < a.n_paths;
+            const uint64_t pidx = keep ? path : 0;          // a valid index for the loads
+            const uint32_t plo = (uint32_t)path, phi = (uint32_t)(path >> 32);
+            const float2 sd = a.seed[pidx];
+            const float aseed = sd.y;                       // dP/dS_i (Asian) or dP/dS_T
+            float gS0 = 0.0f, gk = 0.0f, gth = 0.0f, gxi = 0.0f, grho = 0.0f, gr = 0.0f;
+            float Xb = 0.0f, Vb = 0.0f;                     // adjoints of the state after the step
+            float Xs[kAdjMaxSeg + 1], Vs[kAdjMaxSeg], Zas[kAdjMaxSeg], Zbs[kAdjMaxSeg];
+            for (int seg = (int)a.n_seg - 1; seg >= 0; --seg) {
+                const uint32_t k0 = (uint32_t)seg * a.C;
+                const uint32_t k1 = min(a.N, k0 + a.C);
+                const float2 c0 = a.ckpt[(uint64_t)seg * a.n_paths + pidx];
+                float X = c0.x, V = c0.y;
+                Xs[0] = X;
+                for (uint32_t kk = k0; kk < k1; ++kk) {
+                    float za, zb;
+                    step_normals(a.key, plo, phi, kk, za, zb);
+                    const uint32_t i = kk - k0;
+                    Vs[i] = V; Zas[i] = za; Zbs[i] = zb;
+                    plain_step(X, V, za, zb, k);
+                    Xs[i + 1] = X;
+                }
+                for (int i = (int)(k1 - k0) - 1; i >= 0; --i) {
+                    const uint32_t kp1 = k0 + (uint32_t)i + 1u;
+                    // the payoff's dependence on X_{k+1}
+                    const bool date = MON == MON_NONE ? kp1 == a.N : (kp1 % cs.stride == 0);
+                    if (date) {
+                        const float e = exp_r(Xs[i + 1]);
+                        Xb = fmaf(aseed * cs.S0, e, Xb);
+                        gS0 = fmaf(aseed, e, gS0);
+                    }
+                    const float za = Zas[i], zb = Zbs[i], Vk = Vs[i];
+                    const float Z2 = fmaf(k.rho, za, k.sq * zb);
+                    const bool pos = Vk > 0.0f;
+                    const float Vp = fmaxf(Vk, 0.0f);
+                    const float y = Vp * k.dt;
+                    const float rs = rsqrt_approx(fmaxf(y, 1e-30f));
+                    const float u = y * rs;
+                    const float z2m1 = fmaf(Z2, Z2, -1.0f);
+                    gr = fmaf(Xb, k.dt, gr);
+                    float Vpb = fmaf(-0.5f * k.dt, Xb, -k.kdt * Vb);
+                    const float ub = fmaf(za, Xb, k.xi * Z2 * Vb);
+                    gk = fmaf(Vb, (k.theta - Vp) * k.dt, gk);
+                    gth = fmaf(Vb, k.kdt, gth);
+                    gxi = fmaf(Vb, fmaf(u, Z2, pos ? 0.5f * k.xi * k.dt * z2m1 : 0.0f), gxi);
+                    const float Z2b = Vb * fmaf(k.xi, u, pos ? 0.5f * k.xi * k.xi * k.dt * Z2 : 0.0f);
+                    grho = fmaf(Z2b, fmaf(-k.rho * inv_sq, zb, za), grho);
+                    Vpb = fmaf(ub, 0.5f * k.dt * rs, Vpb);           // du/dV+ = dt / (2u); 0 where u = 0
+                    Vb = pos ? Vb + Vpb : Vb;
+                }
+            }
+            g[q][0] = gS0;
+            g[q][1] = Vb;                                            // dP/dv0 = adjoint of V_0
+            g[q][2] = gk;
+            g[q][3] = gth;
+            g[q][4] = gxi;
+            g[q][5] = grho;
+            g[q][6] = fmaf(-T, sd.x, gr);                            // plus the discount factor
+            if (!keep) {
+#pragma unroll
+                for (int j = 0; j < 7; ++j) g[q][j] = 0.0f;
+            }
+        }
+        double *row = a.rows + tile * 14u;
+#pragma unroll
+        for (int j = 0; j < 7; ++j) {
+            const float sx = warp_sum(g[0][j] + g[1][j]);
+            const float sxx = warp_sum(g[0][j] * g[0][j] + g[1][j] * g[1][j]);
+            if (lane == j) row[j] = (double)sx;
+            if (lane == 7 + j) row[7 + j] = (double)sxx;
+        }
+    }
+}
+
+// Reduce tile rows of `width` columns (sums then sums of squares, E = width/2
+// estimators) in the fixed group order, writing mean[E] then se[E].
+__global__ void reduce_generic_final_kernel(const double *group_sums, uint64_t n_groups, int E,
+                                            double n_paths, double *out)
+{
+    __shared__ double tot[32];
+    const int width = 2 * E;
+    for (int col = threadIdx.x; col < width; col += blockDim.x) {
+        double acc = 0.0;
+        for (uint64_t g = 0; g < n_groups; ++g) acc += group_sums[g * width + col];
+        tot[col] = acc;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < E; e += blockDim.x) {
+        const double mean = tot[e] / n_paths;
+        const double var = (tot[E + e] - n_paths * mean * mean) / (n_paths - 1.0);
+        out[e] = mean;
+        out[E + e] = sqrt(var > 0.0 ? var / n_paths : 0.0);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
@@ -1058,12 +1248,15 @@ int validate_and_prepare(const heston_params *p, const heston_contract *c, uint3
     kd.c4T = 0.25 * p->xi * p->xi * ddt;
     kd.rho = p->rho;
     kd.sq = sq;
+    kd.kappa = p->kappa;
+    kd.theta = p->theta;
     Coef<float> kf;
     kf.v0 = (float)kd.v0; kf.dt = (float)kd.dt; kf.ddt = (float)kd.ddt;
     kf.half_dt = (float)kd.half_dt; kf.r = (float)kd.r; kf.kdt = (float)kd.kdt;
     kf.kth_dt = (float)kd.kth_dt; kf.kth_ddt = (float)kd.kth_ddt; kf.kappa_ddt = (float)kd.kappa_ddt;
     kf.xi = (float)kd.xi; kf.c4 = (float)kd.c4; kf.c4T = (float)kd.c4T;
     kf.rho = (float)kd.rho; kf.sq = (float)kd.sq;
+    kf.kappa = (float)kd.kappa; kf.theta = (float)kd.theta;
 
     out.cs = cs;
     out.csf = csf;
@@ -1688,6 +1881,90 @@ int batch_launch(const heston_batch_plan *plan, const void *d_desc, const heston
     return cudaGetLastError() == cudaSuccess ? HESTON_OK : HESTON_ERR_CUDA;
 }
 
+
+// ---------------------------------------------------------------------------
+// Host: adjoint gradient
+// ---------------------------------------------------------------------------
+struct AdjLayout {
+    uint32_t C, n_seg;
+    size_t off_ckpt, off_seed, off_rows, off_groups, total;
+};
+
+AdjLayout adj_layout(uint64_t n_paths, uint32_t N)
+{
+    AdjLayout L;
+    L.C = (uint32_t)std::ceil(std::sqrt((double)N));
+    if (L.C < 1) L.C = 1;
+    L.n_seg = (N + L.C - 1) / L.C;
+    const uint64_t tiles = tiles_for(n_paths);
+    L.off_ckpt = 0;
+    L.off_seed = align256((size_t)L.n_seg * n_paths * sizeof(float2));
+    L.off_rows = L.off_seed + align256(n_paths * sizeof(float2));
+    L.off_groups = L.off_rows + align256(tiles * 14u * sizeof(double));
+    L.total = L.off_groups + align256(groups_for(tiles) * 14u * sizeof(double));
+    return L;
+}
+
+template <int MON>
+cudaError_t launch_adj_t(bool backward, const Prepared &pp, const AdjLaunch &a, cudaStream_t st)
+{
+    int dev = 0, n_sm = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    if (backward) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, heston_adj_bwd_kernel<MON>, kPathBlock, 0);
+    else          e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, heston_adj_fwd_kernel<MON>, kPathBlock, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    uint64_t grid = std::min<uint64_t>((a.n_tiles + 3) / 4, (uint64_t)n_sm * per_sm);
+    if (pp.opt.grid_ctas) grid = pp.opt.grid_ctas;
+    if (grid < 1) grid = 1;
+    if (backward) heston_adj_bwd_kernel<MON><<<(unsigned)grid, kPathBlock, 0, st>>>(pp.kf, pp.csf, a, (float)pp.cs.T);
+    else          heston_adj_fwd_kernel<MON><<<(unsigned)grid, kPathBlock, 0, st>>>(pp.kf, pp.csf, a);
+    return cudaGetLastError();
+}
+
+int adjoint_enqueue(bool backward, const heston_params *params, const heston_contract *contract,
+                    uint64_t n_paths, uint32_t N, uint64_t seed, const heston_options *opts,
+                    void *ws, size_t ws_bytes, double *d_out)
+{
+    Prepared pp;
+    int rc = validate_and_prepare(params, contract, 1, n_paths, N, opts, pp);
+    if (rc < 0) return rc;
+    if (pp.opt.prec != HESTON_FP32 || pp.opt.trunc != HESTON_TRUNC_FULL || pp.opt.rng != HESTON_RNG_PHILOX)
+        return HESTON_ERR_UNSUPPORTED;
+    const AdjLayout L = adj_layout(n_paths, N);
+    if (L.C > (uint32_t)kAdjMaxSeg) return HESTON_ERR_UNSUPPORTED;
+    if (!d_out) return HESTON_ERR_INVALID_ARG;
+    if (!ws || ((uintptr_t)ws & 255u) || ws_bytes < L.total) return HESTON_ERR_WORKSPACE;
+    DeviceGuard g(pp.opt.device);
+    if (g.err != cudaSuccess) return HESTON_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)pp.opt.cuda_stream;
+    char *b = (char *)ws;
+    AdjLaunch a;
+    a.key = key_of(seed);
+    a.n_paths = n_paths;
+    a.n_tiles = tiles_for(n_paths);
+    a.N = N;
+    a.C = L.C;
+    a.n_seg = L.n_seg;
+    a.ckpt = (float2 *)(b + L.off_ckpt);
+    a.seed = (float2 *)(b + L.off_seed);
+    a.rows = (double *)(b + L.off_rows);
+    const int mon = mon_mode(pp.cs);
+    cudaError_t e = mon == MON_NONE ? launch_adj_t<MON_NONE>(backward, pp, a, st)
+                  : mon == MON_EVERY ? launch_adj_t<MON_EVERY>(backward, pp, a, st)
+                                     : launch_adj_t<MON_STRIDE>(backward, pp, a, st);
+    if (e != cudaSuccess) return HESTON_ERR_CUDA;
+    const int width = backward ? 14 : 2;
+    double *groups = (double *)(b + L.off_groups);
+    const uint64_t ng = groups_for(a.n_tiles);
+    reduce_groups_kernel<<<(unsigned)ng, 64, 0, st>>>(a.rows, a.n_tiles, width, groups);
+    if (cudaGetLastError() != cudaSuccess) return HESTON_ERR_CUDA;
+    reduce_generic_final_kernel<<<1, 32, 0, st>>>(groups, ng, width / 2, (double)n_paths, d_out);
+    return cudaGetLastError() == cudaSuccess ? HESTON_OK : HESTON_ERR_CUDA;
+}
+
 }  // namespace
 
 // Static device scratch of heston_mc_launch_noalloc (see include/heston_mc.h):
@@ -2058,6 +2335,33 @@ int heston_mc_price_greeks_batch(const heston_batch_item *items, uint32_t n_item
         if (status > worst) worst = status;
     }
     return worst;
+}
+
+int heston_adjoint_workspace_bytes(uint64_t n_paths, uint32_t n_steps, size_t *bytes)
+{
+    if (!bytes || n_paths < 2 || n_paths > (1ull << 40) || n_steps == 0) return HESTON_ERR_INVALID_ARG;
+    const AdjLayout L = adj_layout(n_paths, n_steps);
+    if (L.C > (uint32_t)kAdjMaxSeg) return HESTON_ERR_UNSUPPORTED;
+    *bytes = L.total;
+    return HESTON_OK;
+}
+
+int heston_mc_adjoint_forward(const heston_params *params, const heston_contract *contract,
+                              uint64_t n_paths, uint32_t n_steps, uint64_t rng_seed,
+                              const heston_options *opts, void *d_workspace, size_t workspace_bytes_,
+                              double *d_price)
+{
+    return adjoint_enqueue(false, params, contract, n_paths, n_steps, rng_seed, opts, d_workspace,
+                           workspace_bytes_, d_price);
+}
+
+int heston_mc_adjoint_backward(const heston_params *params, const heston_contract *contract,
+                               uint64_t n_paths, uint32_t n_steps, uint64_t rng_seed,
+                               const heston_options *opts, void *d_workspace, size_t workspace_bytes_,
+                               double *d_grad)
+{
+    return adjoint_enqueue(true, params, contract, n_paths, n_steps, rng_seed, opts, d_workspace,
+                           workspace_bytes_, d_grad);
 }
 
 int heston_sobol_directions(uint32_t n_dims, uint32_t *h_out)

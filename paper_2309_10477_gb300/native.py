@@ -122,6 +122,11 @@ def load():
         "heston_mc_launch_batch": ([P(heston_batch_plan), vp, P(heston_options), vp, vp, vp], i32),
         "heston_mc_price_greeks_batch": ([P(heston_batch_item), u32, P(heston_options),
                                           P(heston_result)], i32),
+        "heston_adjoint_workspace_bytes": ([u64, u32, P(sz)], i32),
+        "heston_mc_adjoint_forward": ([P(heston_params), P(heston_contract), u64, u32, u64,
+                                       P(heston_options), vp, sz, vp], i32),
+        "heston_mc_adjoint_backward": ([P(heston_params), P(heston_contract), u64, u32, u64,
+                                        P(heston_options), vp, sz, vp], i32),
         "heston_sobol_directions": ([u32, P(u32)], i32),
         "heston_qmc_tables_bytes": ([u32, P(sz)], i32),
         "heston_qmc_build_tables": ([u32, vp, sz, i32], i32),
@@ -362,3 +367,23 @@ def heston_mc_price_greeks_batch(items, options=None):
     opt = ctypes.byref(options) if options is not None else None
     _check(load().heston_mc_price_greeks_batch(arr, len(items), opt, out))
     return list(out)
+
+
+def heston_adjoint_workspace_bytes(n_paths: int, n_steps: int) -> int:
+    b = ctypes.c_size_t()
+    _check(load().heston_adjoint_workspace_bytes(n_paths, n_steps, ctypes.byref(b)))
+    return b.value
+
+
+def heston_mc_adjoint_forward(params, contract, n_paths, n_steps, rng_seed, options, workspace,
+                              workspace_bytes, price) -> int:
+    return _check(load().heston_mc_adjoint_forward(ctypes.byref(params), ctypes.byref(contract),
+                                                   n_paths, n_steps, rng_seed, ctypes.byref(options),
+                                                   _ptr(workspace), workspace_bytes, _ptr(price)))
+
+
+def heston_mc_adjoint_backward(params, contract, n_paths, n_steps, rng_seed, options, workspace,
+                               workspace_bytes, grad) -> int:
+    return _check(load().heston_mc_adjoint_backward(ctypes.byref(params), ctypes.byref(contract),
+                                                    n_paths, n_steps, rng_seed, ctypes.byref(options),
+                                                    _ptr(workspace), workspace_bytes, _ptr(grad)))

@@ -1,0 +1,89 @@
+"""Adjoint (reverse-mode) gradient kernels vs the oracle's forward-mode
+gradient on identical normals, vs the main kernel's Greek estimators on the
+same paths, and through torch.autograd."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2309_10477_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+BASE = wl.BASE_PARAMS
+NAMES = ("S0", "v0", "kappa", "theta", "xi", "rho", "r")
+
+
+@pytest.fixture(scope="module")
+def nv(cuda_lib):
+    from paper_2309_10477_gb300 import native
+    return native
+
+
+def _run(nv, torch, params, c, n, N, seed):
+    p = nv.make_params(**params)
+    ws_bytes = nv.heston_adjoint_workspace_bytes(n, N)
+    ws = torch.empty(ws_bytes // 8 + 32, dtype=torch.float64, device="cuda")
+    out = torch.empty(2, dtype=torch.float64, device="cuda")
+    g = torch.empty(14, dtype=torch.float64, device="cuda")
+    opts = nv.make_options(prec=nv.HESTON_FP32, stream=torch.cuda.current_stream())
+    nv.heston_mc_adjoint_forward(p, c, n, N, seed, opts, ws, ws_bytes, out)
+    nv.heston_mc_adjoint_backward(p, c, n, N, seed, opts, ws, ws_bytes, g)
+    torch.cuda.synchronize()
+    return out.cpu().numpy(), g.cpu().numpy()
+
+
+@pytest.mark.parametrize("payoff,put,M,N,n", [(0, 0, 0, 64, 1 << 15), (1, 0, 0, 252, 1 << 14),
+                                              (1, 1, 4, 32, (1 << 15) + 37), (0, 1, 0, 7, 5000)])
+def test_adjoint_matches_oracle_forward_mode(nv, payoff, put, M, N, n):
+    import torch
+    c = nv.make_contract(payoff, 100.0, 1.0, put, M)
+    price, g = _run(nv, torch, BASE, c, n, N, 17)
+    om, ose = oracle.mc_gradient(oracle.Params(**BASE), oracle.Contract(payoff, 100.0, 1.0, put, M),
+                                 n, N, 17)
+    gm = np.concatenate([[price[0]], g[:7]])
+    d = np.abs(gm - om)
+    assert (d <= 3 * ose + 1e-9).all(), (d, ose)
+    assert (d <= 1e-4 * np.maximum(1.0, np.abs(om))).all(), (d, om)
+    np.testing.assert_allclose(np.concatenate([[price[1]], g[7:]]), ose, rtol=2e-3, atol=1e-9)
+
+
+def test_adjoint_full_size_against_the_greek_estimators(nv):
+    """252-step Asian call, 2^20 paths: the S0, v0 and r components are the
+    Delta, Vega and Rho of the main kernel on the same paths."""
+    import torch
+    c = nv.make_contract(1, 100.0, 1.0)
+    n, N = 1 << 20, 252
+    price, g = _run(nv, torch, BASE, c, n, N, 42)
+    res = nv.heston_mc_price_greeks_ex(nv.make_params(**BASE), [c], n, N, 42,
+                                       nv.make_options(prec=nv.HESTON_FP32))
+    m, se = nv.results_to_arrays(res)
+    for got, k in ((price[0], 0), (g[0], 1), (g[1], 3), (g[6], 4)):
+        assert abs(got - m[0, k]) <= 1e-4 * max(1.0, abs(m[0, k])), (k, got, m[0, k])
+    assert np.isfinite(g).all()
+
+
+def test_autograd_function(nv):
+    import torch
+    from paper_2309_10477_gb300 import autograd as ag
+    c = nv.make_contract(0, 100.0, 1.0)
+    theta = torch.tensor([BASE[k] for k in NAMES], dtype=torch.float64, requires_grad=True)
+    price = ag.heston_price(theta, c, 1 << 14, 50, 5)
+    (grad,) = torch.autograd.grad(2.0 * price, theta)
+    p, g = _run(nv, torch, BASE, c, 1 << 14, 50, 5)
+    assert float(price) == p[0]
+    assert np.array_equal(grad.numpy(), 2.0 * g[:7])
+
+
+def test_adjoint_rejections(nv):
+    import torch
+    c = nv.make_contract(0, 100.0, 1.0)
+    p = nv.make_params(**BASE)
+    ws = torch.empty(1 << 20, dtype=torch.float64, device="cuda")
+    out = torch.empty(14, dtype=torch.float64, device="cuda")
+    for opts in (nv.make_options(prec=nv.HESTON_FP64), nv.make_options(prec=nv.HESTON_FP32, trunc=1)):
+        with pytest.raises(nv.HestonError) as e:
+            nv.heston_mc_adjoint_forward(p, c, 1024, 10, 1, opts, ws, 8 << 20, out)
+        assert e.value.status == nv.HESTON_ERR_UNSUPPORTED
+    with pytest.raises(nv.HestonError) as e:
+        nv.heston_adjoint_workspace_bytes(1024, 2000)
+    assert e.value.status == nv.HESTON_ERR_UNSUPPORTED
