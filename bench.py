@@ -428,6 +428,73 @@ def run_gpu(args):
                        ("S0", "v0", "kappa", "theta", "xi", "rho", "r"), gv[:7].tolist())),
                    "gradient_se": gv[7:].tolist()}
 
+    # serving: Poisson arrivals of single-contract requests into the native
+    # continuous-batching engine; latency is submit -> result on the host
+    serving = None
+    if not args.no_serve and world == 1:
+        import numpy as np
+        rate, dur = args.serve_rate, args.serve_seconds
+        g = np.random.Generator(np.random.PCG64(2309))
+        n_req = int(rate * dur)
+        arrivals = np.cumsum(g.exponential(1.0 / rate, n_req))
+        reqs = [nv.make_batch_item(nv.make_params(**d["params"]), nv.make_contract(*d["contract"]),
+                                   d["n_paths"], d["n_steps"], w.seed + 7919 * i)
+                for i, d in enumerate(wl.batched_contracts(n_req, seed=2309))]
+        req_path_steps = sum(it.n_paths * it.n_steps for it in reqs)
+        srv = nv.HestonServer(1 << 30, tiles_per_round=args.serve_tiles_per_round, device=local)
+        for t in [srv.submit(it) for it in reqs[:64]]:           # warm-up
+            srv.wait(t, 60000)
+        tickets = [0] * n_req
+        lat = [0.0] * n_req
+        queued_max = [0]
+        submitted = threading.Event()
+
+        def consume():
+            for i in range(n_req):
+                while tickets[i] == 0:
+                    time.sleep(0.0002)
+                r = srv.wait(tickets[i], 120000)
+                assert r is not None and r[0].status >= 0
+                lat[i] = r[1]
+
+        def watch():
+            while not submitted.is_set():
+                st = srv.stats()
+                queued_max[0] = max(queued_max[0], st.queued + st.active)
+                time.sleep(0.01)
+
+        th_c, th_w = threading.Thread(target=consume), threading.Thread(target=watch)
+        st0 = srv.stats()
+        clocks.mark(True)
+        th_c.start()
+        th_w.start()
+        t0 = time.perf_counter()
+        for i in range(n_req):
+            while time.perf_counter() - t0 < arrivals[i]:
+                pass
+            tickets[i] = srv.submit(reqs[i])
+        submit_s = time.perf_counter() - t0
+        submitted.set()
+        th_c.join()
+        wall_s = time.perf_counter() - t0
+        th_w.join()
+        clocks.mark(False)
+        st1 = srv.stats()
+        srv.close()
+        la = np.array(lat) * 1e3
+        serving = {"workload": f"Poisson arrivals at {rate:.0f}/s for {dur:.0f} s ({n_req} requests), "
+                               "each one contract drawn like the batched form (paths 2^U, U~U[14,20]; "
+                               "steps 50..500; European/Asian), FP32",
+                   "offered_path_steps_per_s": req_path_steps / arrivals[-1],
+                   "latency_ms": {"p50": float(np.percentile(la, 50)), "p90": float(np.percentile(la, 90)),
+                                  "p99": float(np.percentile(la, 99)), "max": float(la.max())},
+                   "greek_sets_per_s": n_req / wall_s, "path_steps_per_s": req_path_steps / wall_s,
+                   "drain_after_last_arrival_ms": (wall_s - submit_s) * 1e3,
+                   "max_requests_in_system": queued_max[0],
+                   "rounds": int(st1.rounds - st0.rounds),
+                   "tiles_per_round": args.serve_tiles_per_round,
+                   "memory_peak_bytes": int(st1.memory_peak)}
+
     # end to end through the synchronous host API (host structs in, results out)
     res_arr = (nv.heston_result * nc)()
     carr = (nv.heston_contract * nc)(*contracts)
@@ -496,6 +563,8 @@ def run_gpu(args):
             line["batched_variant"] = batched
         if adjoint is not None:
             line["adjoint_variant"] = adjoint
+        if serving is not None:
+            line["serving_variant"] = serving
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
         print(json.dumps(line), flush=True)
@@ -515,6 +584,10 @@ def main():
     ap.add_argument("--no-qmc", action="store_true", help="skip the quasi-Monte Carlo variant")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 1024-contract form")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint gradient")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serve-rate", type=float, default=2000.0, help="request arrivals per second")
+    ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--serve-tiles-per-round", type=int, default=16384)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--n-paths", type=int, default=0,
                     help="paths per rank (default: the workload's 2^22); small cases for ncu")

@@ -353,6 +353,68 @@ int heston_mc_launch_batch(const heston_batch_plan *plan, const void *d_desc,
 int heston_mc_price_greeks_batch(const heston_batch_item *items, uint32_t n_items,
                                  const heston_options *opts, heston_result *out);
 
+/* ---- serving engine (continuous batching) ---------------------------------- */
+
+/* A request loop over the batched kernel: requests (heston_batch_item, one
+ * contract each) are submitted from any host thread at any time; a server
+ * thread admits them to the device as slots and pool memory free up, and
+ * runs rounds: each round hands every active request a share of
+ * `tiles_per_round` 64-path tiles and launches them together (the
+ * persistent batch kernel with per-request tile offsets), so the work of
+ * requests that arrived at different times overlaps on the GPU.  A request
+ * whose last tile ran is reduced (fixed order) and copied back while the next
+ * round runs.  Every result equals heston_mc_price_greeks_ex of the same item
+ * alone bit for bit (FP32 path; tile rows are fixed by the path index).
+ * Admission is by device memory: a request needs ceil(n_paths/64) * 96 bytes
+ * of the pool until it completes; requests that do not fit wait in FIFO
+ * order; one larger than the whole pool is refused at submit
+ * (HESTON_ERR_NOMEM).  No device code waits on the host: all waiting is on
+ * host condition variables with bounded timeouts. */
+typedef struct heston_server heston_server;
+
+typedef struct {
+    int32_t device;            /* CUDA ordinal, -1 = current */
+    int32_t trunc;             /* heston_trunc for every request */
+    size_t memory_bytes;       /* device pool for the tile rows of admitted requests */
+    uint32_t max_active;       /* requests on the device at once (0 = 1024) */
+    uint32_t reserved;         /* must be 0 */
+    uint64_t tiles_per_round;  /* 64-path tiles per round (0 = 65536) */
+} heston_server_config;
+
+typedef struct {
+    uint64_t submitted, completed, rounds, tiles_done;
+    uint32_t queued, active;
+    size_t memory_in_use, memory_peak;
+} heston_server_stats;
+
+/* Create a server (allocates its device buffers and starts its thread).
+ * HESTON_ERR_INVALID_ARG for a NULL argument, nonzero reserved, unknown
+ * trunc or memory_bytes < 4096; HESTON_ERR_NOMEM if a buffer cannot be
+ * allocated (nothing is left allocated).  The caller owns the handle until
+ * heston_server_destroy. */
+int heston_server_create(const heston_server_config *cfg, heston_server **out);
+
+/* Queue one request (host struct, copied); *ticket identifies it.
+ * Validation as heston_mc_price_greeks_ex; FP32 Philox only. */
+int heston_server_submit(heston_server *s, const heston_batch_item *item, uint64_t *ticket);
+
+/* Non-blocking: returns 1 and fills *out (and *latency_s: submit to result on
+ * the host, seconds; may be NULL) once the request is done, 0 while pending.
+ * A ticket is reported once.  A ticket never issued by this server gives
+ * HESTON_ERR_INVALID_ARG.  A CUDA failure in the request's rounds is
+ * reported as out->status = HESTON_ERR_CUDA. */
+int heston_server_poll(heston_server *s, uint64_t ticket, heston_result *out, double *latency_s);
+
+/* As poll, waiting up to timeout_ms milliseconds. */
+int heston_server_wait(heston_server *s, uint64_t ticket, uint32_t timeout_ms, heston_result *out,
+                       double *latency_s);
+
+int heston_server_stats_get(heston_server *s, heston_server_stats *out);
+
+/* Finish every submitted request, stop the thread, free the device buffers.
+ * Results not yet polled are discarded. */
+int heston_server_destroy(heston_server *s);
+
 /* ---- adjoint (reverse-mode pathwise) parameter gradient -------------------- */
 
 /* Gradient of the discounted price of one contract with respect to

@@ -28,7 +28,11 @@
 #include <cstring>
 #include <deque>
 #include <map>
+#include <chrono>
+#include <condition_variable>
 #include <mutex>
+#include <thread>
+#include <unordered_map>
 #include <vector>
 
 #include "heston_mc.h"
@@ -843,6 +847,7 @@ struct BatchLaunch {
     const BatchItemDev *items;    // caller order
     const uint64_t *work_begin;   // [n_items] first work index of the p-th contract in work order
     const uint32_t *work_item;    // [n_items] contract of the p-th position in work order
+    const uint64_t *work_tile0;   // [n_items] first tile of the p-th position (NULL = 0)
     const uint64_t *group_begin;  // [n_items] (caller order) first group row, for the reductions
     uint32_t n_items;
     uint64_t total_work;
@@ -871,7 +876,7 @@ __global__ void __launch_bounds__(kPathBlock) heston_batch_kernel(BatchLaunch a)
             if (a.work_begin[mid] <= g) lo = mid; else hi = mid;
         }
         const BatchItemDev &it = a.items[a.work_item[lo]];
-        const uint64_t t = g - a.work_begin[lo];
+        const uint64_t t = g - a.work_begin[lo] + (a.work_tile0 ? a.work_tile0[lo] : 0ull);
         const Coef<float> k = it.k;
         const PhiloxKey key = it.key;
         PathState<float> s[2];
@@ -1864,6 +1869,7 @@ int batch_launch(const heston_batch_plan *plan, const void *d_desc, const heston
     a.items = (const BatchItemDev *)(d + L.off_items);
     a.work_begin = (const uint64_t *)(d + L.off_work_begin);
     a.work_item = (const uint32_t *)(d + L.off_work_item);
+    a.work_tile0 = nullptr;
     a.group_begin = (const uint64_t *)(d + L.off_group_begin);
     a.n_items = n;
     a.total_work = plan->total_tiles;
@@ -1963,6 +1969,257 @@ int adjoint_enqueue(bool backward, const heston_params *params, const heston_con
     if (cudaGetLastError() != cudaSuccess) return HESTON_ERR_CUDA;
     reduce_generic_final_kernel<<<1, 32, 0, st>>>(groups, ng, width / 2, (double)n_paths, d_out);
     return cudaGetLastError() == cudaSuccess ? HESTON_OK : HESTON_ERR_CUDA;
+}
+
+
+// ---------------------------------------------------------------------------
+// Serving engine: continuous batching over the persistent batch kernel
+// ---------------------------------------------------------------------------
+}  // namespace
+
+struct heston_server {
+    heston_server_config cfg;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int n_sm = 0, per_sm = 0;
+    // device buffers
+    BatchItemDev *d_slots = nullptr;
+    double *d_pool = nullptr, *d_groups = nullptr, *d_results = nullptr;
+    uint64_t *d_wb[2] = {nullptr, nullptr}, *d_wt[2] = {nullptr, nullptr};
+    uint32_t *d_wi[2] = {nullptr, nullptr};
+    unsigned long long *d_counter = nullptr;
+    // pinned host staging
+    BatchItemDev *h_slots = nullptr;
+    uint64_t *h_wb[2] = {nullptr, nullptr}, *h_wt[2] = {nullptr, nullptr};
+    uint32_t *h_wi[2] = {nullptr, nullptr};
+    double *h_results = nullptr;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    // host state
+    struct Req {
+        uint64_t ticket = 0;
+        BatchItemDev dev;
+        uint64_t tiles = 0, next_tile = 0;
+        size_t bytes = 0, pool_off = 0;
+        int slot = -1;
+        std::chrono::steady_clock::time_point t_submit;
+    };
+    struct Done {
+        heston_result res;
+        double latency;
+    };
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Req> queue;
+    std::vector<Req> slots;                     // by slot; ticket 0 = free
+    std::vector<int> free_slots;
+    std::vector<uint64_t> order;                // active tickets in admission order (slot ids)
+    std::map<size_t, size_t> free_blocks;       // pool offset -> size (bytes)
+    std::unordered_map<uint64_t, Done> done;
+    std::vector<int> pending[2];                // slots finishing in the round on buffer b
+    uint64_t next_ticket = 1;
+    bool stop = false;
+    std::thread th;
+    heston_server_stats st{};
+    size_t pool_bytes = 0;
+};
+
+namespace {
+
+size_t srv_alloc(heston_server *s, size_t bytes)
+{
+    for (auto it = s->free_blocks.begin(); it != s->free_blocks.end(); ++it) {
+        if (it->second >= bytes) {
+            const size_t off = it->first, sz = it->second;
+            s->free_blocks.erase(it);
+            if (sz > bytes) s->free_blocks[off + bytes] = sz - bytes;
+            return off;
+        }
+    }
+    return (size_t)-1;
+}
+
+void srv_free(heston_server *s, size_t off, size_t bytes)
+{
+    auto it = s->free_blocks.emplace(off, bytes).first;
+    auto nx = std::next(it);
+    if (nx != s->free_blocks.end() && it->first + it->second == nx->first) {
+        it->second += nx->second;
+        s->free_blocks.erase(nx);
+    }
+    if (it != s->free_blocks.begin()) {
+        auto pv = std::prev(it);
+        if (pv->first + pv->second == it->first) {
+            pv->second += it->second;
+            s->free_blocks.erase(it);
+        }
+    }
+}
+
+// Pool blocks are multiples of 768 bytes (lcm of the 96-byte tile row and
+// 256-byte alignment), so every block starts on a whole tile row.
+constexpr size_t kPoolUnit = 768;
+size_t srv_req_bytes(uint64_t tiles)
+{
+    const size_t b = tiles * 12u * sizeof(double);
+    return (b + kPoolUnit - 1) / kPoolUnit * kPoolUnit;
+}
+
+// Retire the requests whose reduction ran in the round on buffer b.
+void srv_retire(heston_server *s, int b)
+{
+    if (s->pending[b].empty()) return;
+    const bool failed = cudaEventSynchronize(s->ev[b]) != cudaSuccess;
+    const auto now = std::chrono::steady_clock::now();
+    std::lock_guard<std::mutex> lock(s->mu);
+    for (int slot : s->pending[b]) {
+        heston_server::Req &r = s->slots[slot];
+        heston_server::Done d;
+        const bool gn = r.dev.gamma_nan != 0;
+        fill_results(s->h_results + (size_t)slot * 12u, 1, r.dev.n_paths,
+                     gn ? HESTON_WARN_GAMMA_UNDEFINED : HESTON_OK, &d.res);
+        if (failed) d.res.status = HESTON_ERR_CUDA;
+        d.latency = std::chrono::duration<double>(now - r.t_submit).count();
+        s->done[r.ticket] = d;
+        srv_free(s, r.pool_off, r.bytes);
+        s->st.memory_in_use -= r.bytes;
+        s->st.completed += 1;
+        s->st.active -= 1;
+        s->order.erase(std::find(s->order.begin(), s->order.end(), (uint64_t)slot));
+        r.ticket = 0;
+        s->free_slots.push_back(slot);
+    }
+    s->pending[b].clear();
+    s->cv_done.notify_all();
+}
+
+void srv_loop(heston_server *s)
+{
+    cudaSetDevice(s->device);
+    int b = 0;
+    const uint64_t budget = s->cfg.tiles_per_round;
+    for (;;) {
+        std::vector<int> round_slots;
+        std::vector<uint64_t> round_tiles;
+        std::vector<int> finishing;
+        {
+            std::unique_lock<std::mutex> lock(s->mu);
+            // admission: FIFO while a slot and pool memory are free
+            while (!s->queue.empty() && !s->free_slots.empty()) {
+                heston_server::Req &q = s->queue.front();
+                const size_t off = srv_alloc(s, q.bytes);
+                if (off == (size_t)-1) break;
+                const int slot = s->free_slots.back();
+                s->free_slots.pop_back();
+                q.pool_off = off;
+                q.slot = slot;
+                q.dev.row_begin = off / (12u * sizeof(double));
+                s->h_slots[slot] = q.dev;
+                cudaMemcpyAsync(s->d_slots + slot, s->h_slots + slot, sizeof(BatchItemDev),
+                                cudaMemcpyHostToDevice, s->stream);
+                s->slots[slot] = q;
+                s->order.push_back((uint64_t)slot);
+                s->st.memory_in_use += q.bytes;
+                if (s->st.memory_in_use > s->st.memory_peak) s->st.memory_peak = s->st.memory_in_use;
+                s->st.active += 1;
+                s->st.queued -= 1;
+                s->queue.pop_front();
+            }
+            // round: share the tile budget among requests with tiles left, oldest first
+            uint64_t n_want = 0;
+            for (uint64_t sl : s->order)
+                if (s->slots[sl].next_tile < s->slots[sl].tiles) ++n_want;
+            if (n_want) {
+                const uint64_t quota = std::max<uint64_t>(1, (budget + n_want - 1) / n_want);
+                uint64_t left = budget;
+                for (uint64_t sl : s->order) {
+                    heston_server::Req &r = s->slots[sl];
+                    if (r.next_tile >= r.tiles || left == 0) continue;
+                    const uint64_t take = std::min(std::min(r.tiles - r.next_tile, quota), left);
+                    round_slots.push_back((int)sl);
+                    round_tiles.push_back(take);
+                    left -= take;
+                }
+            }
+            const bool busy = !round_slots.empty() || !s->pending[0].empty() || !s->pending[1].empty();
+            if (!busy) {
+                if (s->stop && s->queue.empty() && s->order.empty()) break;
+                s->cv_work.wait_for(lock, std::chrono::milliseconds(2));
+                continue;
+            }
+        }
+        if (!round_slots.empty()) {
+            // buffer b was last used two rounds ago: its copies and kernels are done
+            srv_retire(s, b);
+            cudaEventSynchronize(s->ev[b]);
+            const uint32_t n = (uint32_t)round_slots.size();
+            uint64_t acc = 0;
+            for (uint32_t p = 0; p < n; ++p) {
+                heston_server::Req &r = s->slots[round_slots[p]];
+                s->h_wb[b][p] = acc;
+                s->h_wi[b][p] = (uint32_t)round_slots[p];
+                s->h_wt[b][p] = r.next_tile;
+                acc += round_tiles[p];
+                r.next_tile += round_tiles[p];
+                if (r.next_tile == r.tiles) finishing.push_back(round_slots[p]);
+            }
+            cudaMemcpyAsync(s->d_wb[b], s->h_wb[b], n * sizeof(uint64_t), cudaMemcpyHostToDevice, s->stream);
+            cudaMemcpyAsync(s->d_wi[b], s->h_wi[b], n * sizeof(uint32_t), cudaMemcpyHostToDevice, s->stream);
+            cudaMemcpyAsync(s->d_wt[b], s->h_wt[b], n * sizeof(uint64_t), cudaMemcpyHostToDevice, s->stream);
+            cudaMemsetAsync(s->d_counter, 0, sizeof(unsigned long long), s->stream);
+            BatchLaunch a;
+            a.items = s->d_slots;
+            a.work_begin = s->d_wb[b];
+            a.work_item = s->d_wi[b];
+            a.work_tile0 = s->d_wt[b];
+            a.group_begin = nullptr;
+            a.n_items = n;
+            a.total_work = acc;
+            a.counter = s->d_counter;
+            a.status = nullptr;
+            a.rows = s->d_pool;
+            const uint64_t grid = std::min<uint64_t>((acc + 3) / 4, (uint64_t)s->n_sm * s->per_sm);
+            if (s->cfg.trunc == HESTON_TRUNC_FULL)
+                heston_batch_kernel<0><<<(unsigned)std::max<uint64_t>(grid, 1), kPathBlock, 0, s->stream>>>(a);
+            else
+                heston_batch_kernel<1><<<(unsigned)std::max<uint64_t>(grid, 1), kPathBlock, 0, s->stream>>>(a);
+            for (int slot : finishing) {
+                const heston_server::Req &r = s->slots[slot];
+                const double *rows = s->d_pool + r.dev.row_begin * 12u;
+                const uint64_t ng = groups_for(r.tiles);
+                reduce_groups_kernel<<<(unsigned)ng, 64, 0, s->stream>>>(rows, r.tiles, 12, s->d_groups);
+                reduce_final_kernel<<<1, 64, 0, s->stream>>>(s->d_groups, ng, 1, (double)r.dev.n_paths,
+                                                             r.dev.gamma_nan, s->d_results + (size_t)slot * 12u);
+                cudaMemcpyAsync(s->h_results + (size_t)slot * 12u, s->d_results + (size_t)slot * 12u,
+                                12u * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+            }
+            cudaEventRecord(s->ev[b], s->stream);
+            {
+                std::lock_guard<std::mutex> lock(s->mu);
+                s->pending[b] = finishing;
+                s->st.rounds += 1;
+                s->st.tiles_done += acc;
+            }
+            // retire the previous round while this one runs
+            srv_retire(s, 1 - b);
+            b = 1 - b;
+        } else {
+            srv_retire(s, b);
+            srv_retire(s, 1 - b);
+        }
+    }
+}
+
+void srv_free_buffers(heston_server *s)
+{
+    cudaFree(s->d_slots); cudaFree(s->d_pool); cudaFree(s->d_groups); cudaFree(s->d_results);
+    cudaFree(s->d_counter);
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(s->d_wb[b]); cudaFree(s->d_wi[b]); cudaFree(s->d_wt[b]);
+        cudaFreeHost(s->h_wb[b]); cudaFreeHost(s->h_wi[b]); cudaFreeHost(s->h_wt[b]);
+        if (s->ev[b]) cudaEventDestroy(s->ev[b]);
+    }
+    cudaFreeHost(s->h_slots); cudaFreeHost(s->h_results);
+    if (s->stream) cudaStreamDestroy(s->stream);
 }
 
 }  // namespace
@@ -2362,6 +2619,129 @@ int heston_mc_adjoint_backward(const heston_params *params, const heston_contrac
 {
     return adjoint_enqueue(true, params, contract, n_paths, n_steps, rng_seed, opts, d_workspace,
                            workspace_bytes_, d_grad);
+}
+
+int heston_server_create(const heston_server_config *cfg, heston_server **out)
+{
+    if (!cfg || !out || cfg->reserved != 0 || cfg->memory_bytes < 4096) return HESTON_ERR_INVALID_ARG;
+    if (cfg->trunc != HESTON_TRUNC_FULL && cfg->trunc != HESTON_TRUNC_PAPER_FLOOR) return HESTON_ERR_INVALID_ARG;
+    heston_server *s = new heston_server();
+    s->cfg = *cfg;
+    if (!s->cfg.max_active) s->cfg.max_active = 1024;
+    if (!s->cfg.tiles_per_round) s->cfg.tiles_per_round = 65536;
+    const uint32_t S = s->cfg.max_active;
+    int e = 0;
+    if (cfg->device >= 0) e |= (int)cudaSetDevice(cfg->device);
+    e |= (int)cudaGetDevice(&s->device);
+    e |= (int)cudaDeviceGetAttribute(&s->n_sm, cudaDevAttrMultiProcessorCount, s->device);
+    e |= (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s->per_sm, heston_batch_kernel<0>, kPathBlock, 0);
+    if (s->per_sm < 1) s->per_sm = 1;
+    e |= (int)cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+    s->pool_bytes = cfg->memory_bytes / kPoolUnit * kPoolUnit;
+    e |= (int)cudaMalloc((void **)&s->d_slots, S * sizeof(BatchItemDev));
+    e |= (int)cudaMalloc((void **)&s->d_pool, s->pool_bytes);
+    e |= (int)cudaMalloc((void **)&s->d_groups, (size_t)groups_for(s->pool_bytes / 96 + 1) * 12 * sizeof(double) + 256);
+    e |= (int)cudaMalloc((void **)&s->d_results, (size_t)S * 12 * sizeof(double));
+    e |= (int)cudaMalloc((void **)&s->d_counter, 256);
+    e |= (int)cudaHostAlloc((void **)&s->h_slots, S * sizeof(BatchItemDev), cudaHostAllocDefault);
+    e |= (int)cudaHostAlloc((void **)&s->h_results, (size_t)S * 12 * sizeof(double), cudaHostAllocDefault);
+    for (int b = 0; b < 2; ++b) {
+        e |= (int)cudaMalloc((void **)&s->d_wb[b], S * sizeof(uint64_t));
+        e |= (int)cudaMalloc((void **)&s->d_wi[b], S * sizeof(uint32_t));
+        e |= (int)cudaMalloc((void **)&s->d_wt[b], S * sizeof(uint64_t));
+        e |= (int)cudaHostAlloc((void **)&s->h_wb[b], S * sizeof(uint64_t), cudaHostAllocDefault);
+        e |= (int)cudaHostAlloc((void **)&s->h_wi[b], S * sizeof(uint32_t), cudaHostAllocDefault);
+        e |= (int)cudaHostAlloc((void **)&s->h_wt[b], S * sizeof(uint64_t), cudaHostAllocDefault);
+        e |= (int)cudaEventCreateWithFlags(&s->ev[b], cudaEventDisableTiming);
+        cudaEventRecord(s->ev[b], s->stream);
+    }
+    if (e != 0) {
+        cudaGetLastError();
+        srv_free_buffers(s);
+        delete s;
+        return HESTON_ERR_NOMEM;
+    }
+    s->slots.resize(S);
+    for (int i = (int)S - 1; i >= 0; --i) s->free_slots.push_back(i);
+    s->free_blocks[0] = s->pool_bytes;
+    s->th = std::thread(srv_loop, s);
+    *out = s;
+    return HESTON_OK;
+}
+
+int heston_server_submit(heston_server *s, const heston_batch_item *item, uint64_t *ticket)
+{
+    if (!s || !item || !ticket) return HESTON_ERR_INVALID_ARG;
+    heston_options o;
+    std::memset(&o, 0, sizeof(o));
+    o.prec = HESTON_FP32;
+    o.trunc = s->cfg.trunc;
+    o.device = -1;
+    std::vector<BatchItemDev> dev;
+    heston_batch_plan plan;
+    const int rc = batch_prepare_items(item, 1, &o, &dev, &plan);
+    if (rc < 0) return rc;
+    heston_server::Req r;
+    r.dev = dev[0];
+    r.tiles = dev[0].n_tiles;
+    r.bytes = srv_req_bytes(r.tiles);
+    if (r.bytes > s->pool_bytes) return HESTON_ERR_NOMEM;
+    r.t_submit = std::chrono::steady_clock::now();
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        if (s->stop) return HESTON_ERR_CANCELLED;
+        r.ticket = s->next_ticket++;
+        *ticket = r.ticket;
+        s->queue.push_back(r);
+        s->st.submitted += 1;
+        s->st.queued += 1;
+    }
+    s->cv_work.notify_one();
+    return HESTON_OK;
+}
+
+int heston_server_wait(heston_server *s, uint64_t ticket, uint32_t timeout_ms, heston_result *out,
+                       double *latency_s)
+{
+    if (!s || !out) return HESTON_ERR_INVALID_ARG;
+    std::unique_lock<std::mutex> lock(s->mu);
+    if (ticket == 0 || ticket >= s->next_ticket) return HESTON_ERR_INVALID_ARG;
+    const bool ok = s->cv_done.wait_for(lock, std::chrono::milliseconds(timeout_ms),
+                                        [&] { return s->done.count(ticket) > 0; });
+    if (!ok) return 0;
+    auto it = s->done.find(ticket);
+    *out = it->second.res;
+    if (latency_s) *latency_s = it->second.latency;
+    s->done.erase(it);
+    return 1;
+}
+
+int heston_server_poll(heston_server *s, uint64_t ticket, heston_result *out, double *latency_s)
+{
+    return heston_server_wait(s, ticket, 0, out, latency_s);
+}
+
+int heston_server_stats_get(heston_server *s, heston_server_stats *out)
+{
+    if (!s || !out) return HESTON_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(s->mu);
+    *out = s->st;
+    return HESTON_OK;
+}
+
+int heston_server_destroy(heston_server *s)
+{
+    if (!s) return HESTON_ERR_INVALID_ARG;
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        s->stop = true;
+    }
+    s->cv_work.notify_all();
+    if (s->th.joinable()) s->th.join();
+    cudaStreamSynchronize(s->stream);
+    srv_free_buffers(s);
+    delete s;
+    return HESTON_OK;
 }
 
 int heston_sobol_directions(uint32_t n_dims, uint32_t *h_out)

@@ -76,6 +76,19 @@ class heston_batch_plan(ctypes.Structure):
                 ("workspace_bytes", ctypes.c_size_t)]
 
 
+class heston_server_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("trunc", ctypes.c_int32), ("memory_bytes", ctypes.c_size_t),
+                ("max_active", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("tiles_per_round", ctypes.c_uint64)]
+
+
+class heston_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("rounds", ctypes.c_uint64), ("tiles_done", ctypes.c_uint64),
+                ("queued", ctypes.c_uint32), ("active", ctypes.c_uint32),
+                ("memory_in_use", ctypes.c_size_t), ("memory_peak", ctypes.c_size_t)]
+
+
 class HestonError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{msg} (status {status})")
@@ -127,6 +140,12 @@ def load():
                                        P(heston_options), vp, sz, vp], i32),
         "heston_mc_adjoint_backward": ([P(heston_params), P(heston_contract), u64, u32, u64,
                                         P(heston_options), vp, sz, vp], i32),
+        "heston_server_create": ([P(heston_server_config), P(vp)], i32),
+        "heston_server_submit": ([vp, P(heston_batch_item), P(u64)], i32),
+        "heston_server_poll": ([vp, u64, P(heston_result), P(ctypes.c_double)], i32),
+        "heston_server_wait": ([vp, u64, u32, P(heston_result), P(ctypes.c_double)], i32),
+        "heston_server_stats_get": ([vp, P(heston_server_stats)], i32),
+        "heston_server_destroy": ([vp], i32),
         "heston_sobol_directions": ([u32, P(u32)], i32),
         "heston_qmc_tables_bytes": ([u32, P(sz)], i32),
         "heston_qmc_build_tables": ([u32, vp, sz, i32], i32),
@@ -387,3 +406,49 @@ def heston_mc_adjoint_backward(params, contract, n_paths, n_steps, rng_seed, opt
     return _check(load().heston_mc_adjoint_backward(ctypes.byref(params), ctypes.byref(contract),
                                                     n_paths, n_steps, rng_seed, ctypes.byref(options),
                                                     _ptr(workspace), workspace_bytes, _ptr(grad)))
+
+
+class HestonServer:
+    """Handle of a native serving engine (heston_server_* in the C ABI)."""
+
+    def __init__(self, memory_bytes: int, max_active: int = 1024, tiles_per_round: int = 0,
+                 trunc: int = HESTON_TRUNC_FULL, device: int = -1):
+        cfg = heston_server_config(device, trunc, memory_bytes, max_active, 0, tiles_per_round)
+        h = ctypes.c_void_p()
+        _check(load().heston_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+
+    def submit(self, item: heston_batch_item) -> int:
+        t = ctypes.c_uint64()
+        _check(load().heston_server_submit(self._h, ctypes.byref(item), ctypes.byref(t)))
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: int = 60000):
+        """(heston_result, latency seconds), or None on timeout."""
+        r = heston_result()
+        lat = ctypes.c_double()
+        rc = _check(load().heston_server_wait(self._h, ticket, timeout_ms, ctypes.byref(r),
+                                              ctypes.byref(lat)))
+        return (r, lat.value) if rc == 1 else None
+
+    def poll(self, ticket: int):
+        r = heston_result()
+        lat = ctypes.c_double()
+        rc = _check(load().heston_server_poll(self._h, ticket, ctypes.byref(r), ctypes.byref(lat)))
+        return (r, lat.value) if rc == 1 else None
+
+    def stats(self) -> heston_server_stats:
+        st = heston_server_stats()
+        _check(load().heston_server_stats_get(self._h, ctypes.byref(st)))
+        return st
+
+    def close(self):
+        if self._h:
+            _check(load().heston_server_destroy(self._h))
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
