@@ -6,7 +6,8 @@ path (``paper_2309_10477_gb300``) never imports it and shares no code with it.
 
 Contents:
   * ``heston_oracle.c`` -- Philox4x32-10, Box-Muller, the Milstein scheme of
-    Sec. 2.4.2 with full truncation or the paper's floor, pathwise tangents,
+    Sec. 2.4.2 with full truncation or the paper's floor, the Euler scheme of
+    Sec. 2.4.1, Andersen's QE scheme (named in Sec. 5), pathwise tangents,
     per-path estimators and the Monte Carlo driver of Sec. 2.5 (plain C, FP64).
   * ``closed_form`` -- Black-Scholes and the Heston characteristic-function
     price and Greeks (the "real price" the paper quotes in Sec. 3).
@@ -39,6 +40,7 @@ PATH_FIELDS = ("X", "V", "X_v", "V_v", "X_T", "V_T", "sumS", "sumtS", "sumS_Xv",
                "sumS_XT", "GE", "QE", "GA", "QA", "minabsV")
 ESTIMATORS = ("price", "delta", "gamma", "vega", "rho", "theta")
 TRUNC_FULL, TRUNC_FLOOR = 0, 1
+SCHEME_MILSTEIN, SCHEME_EULER, SCHEME_QE = 0, 1, 2
 EUROPEAN, ASIAN = 0, 1
 
 
@@ -80,15 +82,15 @@ def _load():
         lib.orc_normal_pair.argtypes = [u64, u64, u32, u32, P(d), P(d)]
         lib.orc_path_normals.argtypes = [u64, u64, u32, u32, P(d), P(d)]
         lib.orc_mc_sums.argtypes = [P(_Params), P(_Contract), u32, u64, u64, u32, u64, i32, i32,
-                                    P(d), P(d)]
+                                    i32, P(d), P(d)]
         lib.orc_mc_sums.restype = i32
         lib.orc_debug_paths.argtypes = [P(_Params), P(_Contract), u32, P(u64), u64, u32, u64, i32,
-                                        P(d), P(d)]
+                                        i32, P(d), P(d)]
         lib.orc_debug_paths.restype = i32
-        lib.orc_path_from_normals.argtypes = [P(_Params), P(_Contract), u32, u32, i32, P(d), P(d),
+        lib.orc_path_from_normals.argtypes = [P(_Params), P(_Contract), u32, u32, i32, i32, P(d), P(d),
                                               P(d), P(d), P(d), P(d)]
         lib.orc_path_from_normals.restype = i32
-        lib.orc_paths_from_normals.argtypes = [P(_Params), P(_Contract), u32, u32, i32, u64,
+        lib.orc_paths_from_normals.argtypes = [P(_Params), P(_Contract), u32, u32, i32, i32, u64,
                                                P(d), P(d), P(d), P(d)]
         lib.orc_paths_from_normals.restype = i32
         lib.orc_mc_gradient.argtypes = [P(_Params), P(_Contract), u64, u32, u64, P(d), P(d)]
@@ -173,7 +175,7 @@ def _check_rc(rc):
 
 
 def mc_sums(params: Params, contracts, n_paths, n_steps, seed, trunc=TRUNC_FULL,
-            path_begin=0, n_threads=0):
+            path_begin=0, n_threads=0, scheme=SCHEME_MILSTEIN):
     """Sums (sum_x, sum_x^2) per contract and estimator, shape (C, 6) each."""
     lib = _load()
     cs = _contracts(contracts)
@@ -182,7 +184,7 @@ def mc_sums(params: Params, contracts, n_paths, n_steps, seed, trunc=TRUNC_FULL,
     s2 = np.zeros(E)
     p = params._c()
     rc = lib.orc_mc_sums(ctypes.byref(p), cs, len(contracts), path_begin, n_paths, n_steps, seed,
-                         trunc, n_threads, _dptr(s), _dptr(s2))
+                         trunc, scheme, n_threads, _dptr(s), _dptr(s2))
     _check_rc(rc)
     return s.reshape(-1, 6), s2.reshape(-1, 6)
 
@@ -195,13 +197,14 @@ def mean_se(s, s2, n):
 
 
 def mc_price_greeks(params: Params, contracts, n_paths, n_steps, seed, trunc=TRUNC_FULL,
-                    n_threads=0):
+                    n_threads=0, scheme=SCHEME_MILSTEIN):
     """Estimates and SEs per contract: two (C, 6) arrays in ESTIMATORS order."""
-    s, s2 = mc_sums(params, contracts, n_paths, n_steps, seed, trunc, 0, n_threads)
+    s, s2 = mc_sums(params, contracts, n_paths, n_steps, seed, trunc, 0, n_threads, scheme)
     return mean_se(s, s2, n_paths)
 
 
-def debug_paths(params: Params, contracts, paths, n_steps, seed, trunc=TRUNC_FULL):
+def debug_paths(params: Params, contracts, paths, n_steps, seed, trunc=TRUNC_FULL,
+                scheme=SCHEME_MILSTEIN):
     """Per-path records (count, 15) in PATH_FIELDS order and estimators (count, C, 6)."""
     lib = _load()
     paths = np.ascontiguousarray(np.asarray(paths, dtype=np.uint64))
@@ -211,12 +214,12 @@ def debug_paths(params: Params, contracts, paths, n_steps, seed, trunc=TRUNC_FUL
     p = params._c()
     rc = lib.orc_debug_paths(ctypes.byref(p), cs, len(contracts),
                              paths.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), len(paths),
-                             n_steps, seed, trunc, _dptr(rec), _dptr(est))
+                             n_steps, seed, trunc, scheme, _dptr(rec), _dptr(est))
     _check_rc(rc)
     return rec, est
 
 
-def path_from_normals(params: Params, contracts, za, zb, trunc=TRUNC_FULL):
+def path_from_normals(params: Params, contracts, za, zb, trunc=TRUNC_FULL, scheme=SCHEME_MILSTEIN):
     """One path from given normals: (record, estimators (C, 6), X_k, V_k for k=0..N)."""
     lib = _load()
     za = np.ascontiguousarray(za, dtype=np.float64)
@@ -228,13 +231,13 @@ def path_from_normals(params: Params, contracts, za, zb, trunc=TRUNC_FULL):
     tx = np.zeros(n + 1)
     tv = np.zeros(n + 1)
     p = params._c()
-    rc = lib.orc_path_from_normals(ctypes.byref(p), cs, len(contracts), n, trunc, _dptr(za),
+    rc = lib.orc_path_from_normals(ctypes.byref(p), cs, len(contracts), n, trunc, scheme, _dptr(za),
                                    _dptr(zb), _dptr(rec), _dptr(est), _dptr(tx), _dptr(tv))
     _check_rc(rc)
     return rec, est, tx, tv
 
 
-def paths_from_normals(params: Params, contracts, za, zb, trunc=TRUNC_FULL):
+def paths_from_normals(params: Params, contracts, za, zb, trunc=TRUNC_FULL, scheme=SCHEME_MILSTEIN):
     """Many paths from given normals (n_paths, N): records (n, 15) and estimators (n, C, 6)."""
     lib = _load()
     za = np.ascontiguousarray(za, dtype=np.float64)
@@ -244,7 +247,7 @@ def paths_from_normals(params: Params, contracts, za, zb, trunc=TRUNC_FULL):
     rec = np.zeros((n, len(PATH_FIELDS)))
     est = np.zeros((n, len(contracts), 6))
     p = params._c()
-    rc = lib.orc_paths_from_normals(ctypes.byref(p), cs, len(contracts), N, trunc, n, _dptr(za),
+    rc = lib.orc_paths_from_normals(ctypes.byref(p), cs, len(contracts), N, trunc, scheme, n, _dptr(za),
                                     _dptr(zb), _dptr(rec), _dptr(est))
     _check_rc(rc)
     return rec, est

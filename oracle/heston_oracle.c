@@ -20,6 +20,14 @@
  *     approximation under Heston model"), with exactly N integer steps and
  *     either full truncation (Lord, Koekkoek, van Dijk 2010) or the paper's
  *     floor max(V, 0) after each update.
+ *   - Two more schemes on the same normals: the Euler scheme of Sec. 2.4.1
+ *     (the Milstein step without its xi^2 dt (Z^2 - 1) / 4 term; same
+ *     truncation choices), and Andersen's quadratic-exponential (QE) scheme,
+ *     which the paper names as the next method to try (Sec. 5), written from
+ *     L. Andersen, "Simple and efficient simulation of the Heston stochastic
+ *     volatility model", J. Comput. Finance 11(3), 2008 (Sec. 3.2.3 and the
+ *     log-price step of its Sec. 4.2 with gamma1 = gamma2 = 1/2, no
+ *     martingale correction).
  *   - The Monte Carlo estimator of the Algorithm "Monte Carlo option pricing
  *     estimation" (Sec. 2.5), extended to the pathwise Greeks of
  *     Eq. (euro_pw) and Eq. (asian_pw) (pathwise method, Sec. 2).  Asian Rho uses the
@@ -63,6 +71,9 @@ typedef struct {
 } orc_contract;
 
 enum { ORC_TRUNC_FULL = 0, ORC_TRUNC_FLOOR = 1 };
+enum { ORC_SCHEME_MILSTEIN = 0, ORC_SCHEME_EULER = 1, ORC_SCHEME_QE = 2 };
+/* QE switching level of psi = s^2 / m^2 (Andersen's suggested value). */
+static const double ORC_QE_PSI_C = 1.5;
 
 /* ------------------------------------------------------------------ */
 /* Philox4x32-10 (SC'11 paper, Sec. 4 "Philox")                        */
@@ -139,7 +150,7 @@ void orc_path_normals(uint64_t seed, uint64_t path, uint32_t n_steps, uint32_t s
 }
 
 /* ------------------------------------------------------------------ */
-/* One Milstein path with tangents (Sec. 2.4.2)                        */
+/* One path with tangents: Milstein (Sec. 2.4.2), Euler (Sec. 2.4.1), QE */
 /* ------------------------------------------------------------------ */
 
 /* Per-path record.  X = ln(S/S0); V = variance state; *_v = d/dv0 and
@@ -151,94 +162,208 @@ typedef struct {
     double X, V, X_v, V_v, X_T, V_T;
     double sumS, sumtS, sumS_Xv, sumS_XT;   /* sum S_ti, sum t_i S_ti, sum S_ti X_v(t_i), sum S_ti X_T(t_i) */
     double GE, QE, GA, QA;
-    double minabsV;                         /* min |value deciding a truncation branch| (flip classification) */
+    double minabsV;                         /* smallest distance to a branch decision (flip classification) */
 } orc_path;
 
 /* Number of doubles in orc_path, for the flat per-path dump. */
 #define ORC_PATH_DOUBLES 15
 
+/* Standard normal lower tail Phi(x), from the C library's erfc. */
+static double orc_norm_cdf(double x) { return 0.5 * erfc(-x / sqrt(2.0)); }
+
+/* One QE step of the variance (Andersen 2008, Sec. 3.2.3) with its v0- and
+ * T-tangents.  Given V = V(t) >= 0, the exact conditional mean and variance
+ * of the CIR process over dt are
+ *   m  = theta + (V - theta) e^{-kappa dt},
+ *   s2 = V xi^2 e^{-kappa dt} (1 - e^{-kappa dt}) / kappa
+ *        + theta xi^2 (1 - e^{-kappa dt})^2 / (2 kappa),
+ * and psi = s2 / m^2.  For psi <= psi_c the next value is a (b + Zv)^2 with
+ *   b^2 = 2/psi - 1 + sqrt(2/psi) sqrt(2/psi - 1),  a = m / (1 + b^2);
+ * otherwise it is 0 when Uv <= p and ln((1 - p) / (1 - Uv)) / beta above,
+ *   p = (psi - 1) / (psi + 1),  beta = (1 - p) / m.
+ * Zv = Za and Uv = Phi(Za): one uniform drives both branches (only one is
+ * used per step).  *margin receives the distance, in variance units, of
+ * this step from its branch decisions. */
+static void orc_qe_variance(const orc_params *p, double dt, double ddt, double V, double V_v,
+                            double V_T, double Za, double *Vn, double *Vn_v, double *Vn_T,
+                            double *margin)
+{
+    const double kap = p->kappa, th = p->theta, xi2 = p->xi * p->xi;
+    const double E = exp(-kap * dt);
+    const double E_T = -kap * E * ddt;                         /* dE/dT */
+    /* g = (1 - E) / kappa, with its kappa -> 0 limit dt; dg/dT = E / N. */
+    const double g = kap > 0.0 ? -expm1(-kap * dt) / kap : dt;
+    const double g_T = E * ddt;
+    const double omE = kap > 0.0 ? -expm1(-kap * dt) : 0.0;    /* 1 - E */
+
+    const double m = th + (V - th) * E;
+    const double m_v = V_v * E;
+    const double m_T = V_T * E + (V - th) * E_T;
+    const double s2 = V * xi2 * E * g + 0.5 * th * xi2 * omE * g;
+    const double s2_v = V_v * xi2 * E * g;
+    const double s2_T = xi2 * (V_T * E * g + V * (E_T * g + E * g_T))
+                        + 0.5 * th * xi2 * (-E_T * g + omE * g_T);
+    const double psi = s2 / (m * m);
+    const double psi_v = s2_v / (m * m) - 2.0 * s2 * m_v / (m * m * m);
+    const double psi_T = s2_T / (m * m) - 2.0 * s2 * m_T / (m * m * m);
+    double mg = m * fabs(psi - ORC_QE_PSI_C) / ORC_QE_PSI_C;
+
+    if (psi <= ORC_QE_PSI_C) {
+        /* quadratic branch */
+        const double y = 2.0 / psi;
+        const double y_v = -2.0 * psi_v / (psi * psi);
+        const double y_T = -2.0 * psi_T / (psi * psi);
+        const double root = sqrt(y) * sqrt(y - 1.0);
+        const double b2 = y - 1.0 + root;
+        const double db2_dy = 1.0 + (2.0 * y - 1.0) / (2.0 * root);
+        const double b = sqrt(b2);
+        const double a = m / (1.0 + b2);
+        const double b2_v = db2_dy * y_v, b2_T = db2_dy * y_T;
+        const double b_v = b2_v / (2.0 * b), b_T = b2_T / (2.0 * b);
+        const double a_v = m_v / (1.0 + b2) - m * b2_v / ((1.0 + b2) * (1.0 + b2));
+        const double a_T = m_T / (1.0 + b2) - m * b2_T / ((1.0 + b2) * (1.0 + b2));
+        *Vn = a * (b + Za) * (b + Za);
+        *Vn_v = a_v * (b + Za) * (b + Za) + 2.0 * a * (b + Za) * b_v;
+        *Vn_T = a_T * (b + Za) * (b + Za) + 2.0 * a * (b + Za) * b_T;
+    } else {
+        /* exponential branch: Psi^{-1}(Uv) with the mass p at zero */
+        const double pr = (psi - 1.0) / (psi + 1.0);
+        const double pr_v = 2.0 * psi_v / ((psi + 1.0) * (psi + 1.0));
+        const double pr_T = 2.0 * psi_T / ((psi + 1.0) * (psi + 1.0));
+        const double beta = (1.0 - pr) / m;
+        const double Uv = orc_norm_cdf(Za);
+        const double one_m_U = orc_norm_cdf(-Za);              /* 1 - Uv without cancellation */
+        const double dm = m * fabs(one_m_U - (1.0 - pr)) / (1.0 - pr);
+        if (dm < mg) mg = dm;
+        if (Uv <= pr) {
+            *Vn = 0.0; *Vn_v = 0.0; *Vn_T = 0.0;
+        } else {
+            const double L = log((1.0 - pr) / one_m_U);
+            *Vn = L / beta;
+            /* V' = m L / (1 - p), L = ln(1 - p) - ln(1 - Uv) */
+            *Vn_v = m_v * L / (1.0 - pr) + m * pr_v * (L - 1.0) / ((1.0 - pr) * (1.0 - pr));
+            *Vn_T = m_T * L / (1.0 - pr) + m * pr_T * (L - 1.0) / ((1.0 - pr) * (1.0 - pr));
+        }
+    }
+    *margin = mg;
+}
+
 /* Simulate one path from the given normals.  Za, Zb: independent N(0,1)
  * draws per step (Algorithm "Generation of two correlated Normal random
  * variables", step 1).  M = number of Asian dates (N % M == 0).
- * traj_X / traj_V, when non-NULL, receive X_k, V_k for k = 0..N. */
-void orc_milstein_path(const orc_params *p, double T, uint32_t N, uint32_t M, int trunc,
-                       const double *Za, const double *Zb, orc_path *out,
-                       double *traj_X, double *traj_V)
+ * scheme: Milstein, Euler (trunc applies to both) or QE (trunc ignored:
+ * its variance is never negative).  traj_X / traj_V, when non-NULL,
+ * receive X_k, V_k for k = 0..N. */
+void orc_scheme_path(const orc_params *p, double T, uint32_t N, uint32_t M, int trunc, int scheme,
+                     const double *Za, const double *Zb, orc_path *out,
+                     double *traj_X, double *traj_V)
 {
     const double dt = T / (double)N;
     const double ddt = 1.0 / (double)N;            /* d(dt)/dT */
     const double sq = sqrt(1.0 - p->rho * p->rho);
     const uint32_t stride = N / M;                  /* steps between monitoring dates */
+    /* the Milstein term xi^2 dt (Z2^2 - 1) / 4 is what Euler leaves out */
+    const double mil_on = scheme == ORC_SCHEME_MILSTEIN ? 1.0 : 0.0;
 
     double X = 0.0, V = p->v0;
     double X_v = 0.0, V_v = 1.0;                    /* dX/dv0, dV/dv0 at t = 0 */
     double X_T = 0.0, V_T = 0.0;                    /* dX/dT,  dV/dT  at t = 0 */
     double sumS = 0.0, sumtS = 0.0, sumS_Xv = 0.0, sumS_XT = 0.0;
     double GE = 0.0, QE = 0.0, GA = 0.0, QA = 0.0;
-    double minabsV = fabs(V);
+    double minabsV = scheme == ORC_SCHEME_QE ? INFINITY : fabs(V);
 
     if (traj_X) { traj_X[0] = X; traj_V[0] = V; }
 
     for (uint32_t k = 0; k < N; ++k) {
-        /* Correlation step: Z1 = Za, Z2 = rho Z1 + sqrt(1 - rho^2) Zb.
-         * W is the component of Z1 orthogonal to Z2 (used by Gamma):
-         * Z1 = rho Z2 + sqrt(1 - rho^2) W. */
-        const double Z1 = Za[k];
-        const double Z2 = p->rho * Z1 + sq * Zb[k];
-        const double W = sq * Za[k] - p->rho * Zb[k];
-
-        /* Positive part used by drift and diffusion.  Under the paper's
-         * floor V is never negative, so Vp == V there. */
-        const int pos = V > 0.0;
-        const double Vp = pos ? V : 0.0;
-        const double Vp_v = pos ? V_v : 0.0;
-        const double Vp_T = pos ? V_T : 0.0;
-        const double u = sqrt(Vp * dt);              /* sqrt(V dt) */
-        /* d u = d(Vp dt) / (2 u); zero where u == 0. */
-        const double u_v = (u > 0.0) ? (Vp_v * dt) / (2.0 * u) : 0.0;
-        const double u_T = (u > 0.0) ? (Vp_T * dt + Vp * ddt) / (2.0 * u) : 0.0;
-
-        /* Gamma weights accumulate before this step's update. */
-        GE += u * W;
-        QE += Vp * dt;
-        if (k < stride) { GA += u * W; QA += Vp * dt; }
-
-        /* ln S step with the pre-update variance:
-         * ln S_{t+dt} = ln S_t + (r - V/2) dt + sqrt(V dt) Z1. */
-        const double Xn = X + (p->r - 0.5 * Vp) * dt + u * Z1;
-        const double Xn_v = X_v - 0.5 * Vp_v * dt + u_v * Z1;
-        const double Xn_T = X_T + (p->r - 0.5 * Vp) * ddt - 0.5 * Vp_T * dt + u_T * Z1;
-
-        /* V step: V + kappa (theta - V) dt + xi sqrt(V dt) Z2 + xi^2 dt (Z2^2 - 1) / 4. */
-        double Vn, Vn_v, Vn_T;
-        double branch;              /* the value whose sign picks the next branch */
-        if (trunc == ORC_TRUNC_FULL) {
-            /* Full truncation: the state keeps its sign; drift, diffusion and
-             * the Milstein term (which comes from the diffusion) see V+. */
-            const double mil = pos ? 1.0 : 0.0;
-            Vn = V + p->kappa * (p->theta - Vp) * dt + p->xi * u * Z2
-                 + 0.25 * p->xi * p->xi * dt * (Z2 * Z2 - 1.0) * mil;
-            Vn_v = V_v - p->kappa * Vp_v * dt + p->xi * u_v * Z2;
-            Vn_T = V_T + p->kappa * (p->theta - Vp) * ddt - p->kappa * Vp_T * dt
-                   + p->xi * u_T * Z2 + 0.25 * p->xi * p->xi * ddt * (Z2 * Z2 - 1.0) * mil;
-            branch = Vn;
+        double Xn, Xn_v, Xn_T, Vn, Vn_v, Vn_T;
+        double branch;              /* distance from the branch decision of this step */
+        if (scheme == ORC_SCHEME_QE) {
+            /* Variance first (Zv = Za), then ln S from both variances with
+             * the independent normal Zb (Andersen 2008, Sec. 4.2):
+             * ln S' = ln S + r dt + K0 + K1 V + K2 V' + sqrt(K3 V + K4 V') Zb,
+             * K0 = -rho kappa theta dt / xi, K1 = dt/2 (kappa rho / xi - 1/2) - rho / xi,
+             * K2 = dt/2 (kappa rho / xi - 1/2) + rho / xi, K3 = K4 = dt/2 (1 - rho^2). */
+            orc_qe_variance(p, dt, ddt, V, V_v, V_T, Za[k], &Vn, &Vn_v, &Vn_T, &branch);
+            const double K0 = -p->rho * p->kappa * p->theta * dt / p->xi;
+            const double K0_T = -p->rho * p->kappa * p->theta * ddt / p->xi;
+            const double K1 = 0.5 * dt * (p->kappa * p->rho / p->xi - 0.5) - p->rho / p->xi;
+            const double K2 = 0.5 * dt * (p->kappa * p->rho / p->xi - 0.5) + p->rho / p->xi;
+            const double K12_T = 0.5 * ddt * (p->kappa * p->rho / p->xi - 0.5);
+            const double K3 = 0.5 * dt * (1.0 - p->rho * p->rho);
+            const double K3_T = 0.5 * ddt * (1.0 - p->rho * p->rho);
+            const double sig = sqrt(K3 * (V + Vn));
+            Xn = X + p->r * dt + K0 + K1 * V + K2 * Vn + sig * Zb[k];
+            Xn_v = X_v + K1 * V_v + K2 * Vn_v
+                   + (sig > 0.0 ? K3 * (V_v + Vn_v) / (2.0 * sig) : 0.0) * Zb[k];
+            Xn_T = X_T + p->r * ddt + K0_T + K12_T * V + K1 * V_T + K12_T * Vn + K2 * Vn_T
+                   + (sig > 0.0 ? (K3_T * (V + Vn) + K3 * (V_T + Vn_T)) / (2.0 * sig) : 0.0) * Zb[k];
+            /* Gamma weights: given the variance path, the ln S noise of the
+             * step is sq * ut * Zb with ut = sqrt(dt (V + V') / 2), and Zb
+             * does not move the variance. */
+            const double ut = sqrt(0.5 * dt * (V + Vn));
+            GE += ut * Zb[k];
+            QE += 0.5 * dt * (V + Vn);
+            if (k < stride) { GA += ut * Zb[k]; QA += 0.5 * dt * (V + Vn); }
         } else {
-            /* The paper's scheme as printed: update with V, then V = max(V, 0). */
-            const double Vt = V + p->kappa * (p->theta - V) * dt + p->xi * u * Z2
-                              + 0.25 * p->xi * p->xi * dt * (Z2 * Z2 - 1.0);
-            const double Vt_v = V_v - p->kappa * V_v * dt + p->xi * u_v * Z2;
-            const double Vt_T = V_T + p->kappa * (p->theta - V) * ddt - p->kappa * V_T * dt
-                                + p->xi * u_T * Z2 + 0.25 * p->xi * p->xi * ddt * (Z2 * Z2 - 1.0);
-            const int keep = Vt > 0.0;
-            Vn = keep ? Vt : 0.0;
-            Vn_v = keep ? Vt_v : 0.0;
-            Vn_T = keep ? Vt_T : 0.0;
-            branch = Vt;
+            /* Correlation step: Z1 = Za, Z2 = rho Z1 + sqrt(1 - rho^2) Zb.
+             * W is the component of Z1 orthogonal to Z2 (used by Gamma):
+             * Z1 = rho Z2 + sqrt(1 - rho^2) W. */
+            const double Z1 = Za[k];
+            const double Z2 = p->rho * Z1 + sq * Zb[k];
+            const double W = sq * Za[k] - p->rho * Zb[k];
+
+            /* Positive part used by drift and diffusion.  Under the paper's
+             * floor V is never negative, so Vp == V there. */
+            const int pos = V > 0.0;
+            const double Vp = pos ? V : 0.0;
+            const double Vp_v = pos ? V_v : 0.0;
+            const double Vp_T = pos ? V_T : 0.0;
+            const double u = sqrt(Vp * dt);              /* sqrt(V dt) */
+            /* d u = d(Vp dt) / (2 u); zero where u == 0. */
+            const double u_v = (u > 0.0) ? (Vp_v * dt) / (2.0 * u) : 0.0;
+            const double u_T = (u > 0.0) ? (Vp_T * dt + Vp * ddt) / (2.0 * u) : 0.0;
+
+            /* Gamma weights accumulate before this step's update. */
+            GE += u * W;
+            QE += Vp * dt;
+            if (k < stride) { GA += u * W; QA += Vp * dt; }
+
+            /* ln S step with the pre-update variance:
+             * ln S_{t+dt} = ln S_t + (r - V/2) dt + sqrt(V dt) Z1. */
+            Xn = X + (p->r - 0.5 * Vp) * dt + u * Z1;
+            Xn_v = X_v - 0.5 * Vp_v * dt + u_v * Z1;
+            Xn_T = X_T + (p->r - 0.5 * Vp) * ddt - 0.5 * Vp_T * dt + u_T * Z1;
+
+            /* V step: V + kappa (theta - V) dt + xi sqrt(V dt) Z2 [+ xi^2 dt (Z2^2 - 1) / 4]. */
+            if (trunc == ORC_TRUNC_FULL) {
+                /* Full truncation: the state keeps its sign; drift, diffusion and
+                 * the Milstein term (which comes from the diffusion) see V+. */
+                const double mil = pos ? mil_on : 0.0;
+                Vn = V + p->kappa * (p->theta - Vp) * dt + p->xi * u * Z2
+                     + 0.25 * p->xi * p->xi * dt * (Z2 * Z2 - 1.0) * mil;
+                Vn_v = V_v - p->kappa * Vp_v * dt + p->xi * u_v * Z2;
+                Vn_T = V_T + p->kappa * (p->theta - Vp) * ddt - p->kappa * Vp_T * dt
+                       + p->xi * u_T * Z2 + 0.25 * p->xi * p->xi * ddt * (Z2 * Z2 - 1.0) * mil;
+                branch = fabs(Vn);
+            } else {
+                /* The paper's scheme as printed: update with V, then V = max(V, 0). */
+                const double Vt = V + p->kappa * (p->theta - V) * dt + p->xi * u * Z2
+                                  + 0.25 * p->xi * p->xi * dt * (Z2 * Z2 - 1.0) * mil_on;
+                const double Vt_v = V_v - p->kappa * V_v * dt + p->xi * u_v * Z2;
+                const double Vt_T = V_T + p->kappa * (p->theta - V) * ddt - p->kappa * V_T * dt
+                                    + p->xi * u_T * Z2
+                                    + 0.25 * p->xi * p->xi * ddt * (Z2 * Z2 - 1.0) * mil_on;
+                const int keep = Vt > 0.0;
+                Vn = keep ? Vt : 0.0;
+                Vn_v = keep ? Vt_v : 0.0;
+                Vn_T = keep ? Vt_T : 0.0;
+                branch = fabs(Vt);
+            }
         }
 
         X = Xn; X_v = Xn_v; X_T = Xn_T;
         V = Vn; V_v = Vn_v; V_T = Vn_T;
-        if (fabs(branch) < minabsV) minabsV = fabs(branch);
+        if (branch < minabsV) minabsV = branch;
         if (traj_X) { traj_X[k + 1] = X; traj_V[k + 1] = V; }
 
         /* Asian monitoring date t_i = (k+1) dt when (k+1) is a multiple of the stride. */
@@ -256,6 +381,16 @@ void orc_milstein_path(const orc_params *p, double T, uint32_t N, uint32_t M, in
     out->sumS = sumS; out->sumtS = sumtS; out->sumS_Xv = sumS_Xv; out->sumS_XT = sumS_XT;
     out->GE = GE; out->QE = QE; out->GA = GA; out->QA = QA;
     out->minabsV = minabsV;
+}
+
+/* Scheme arguments a driver accepts: QE needs kappa, theta, xi > 0 (its
+ * moments divide by kappa and xi, and m = 0 would make psi undefined). */
+static int orc_scheme_ok(const orc_params *p, int trunc, int scheme)
+{
+    if (trunc != ORC_TRUNC_FULL && trunc != ORC_TRUNC_FLOOR) return 0;
+    if (scheme == ORC_SCHEME_MILSTEIN || scheme == ORC_SCHEME_EULER) return 1;
+    if (scheme != ORC_SCHEME_QE) return 0;
+    return p->kappa > 0.0 && p->theta > 0.0 && p->xi > 0.0;
 }
 
 /* ------------------------------------------------------------------ */
@@ -338,9 +473,9 @@ void orc_estimators(const orc_params *p, const orc_contract *c, uint32_t N,
  * Returns 0, or -1 on invalid input. */
 int orc_mc_sums(const orc_params *p, const orc_contract *contracts, uint32_t n_contracts,
                 uint64_t path_begin, uint64_t n_paths, uint32_t N, uint64_t seed, int trunc,
-                int n_threads, double *sum, double *sumsq)
+                int scheme, int n_threads, double *sum, double *sumsq)
 {
-    if (n_contracts == 0 || N == 0) return -1;
+    if (n_contracts == 0 || N == 0 || !orc_scheme_ok(p, trunc, scheme)) return -1;
     const double T = contracts[0].T;
     uint32_t M = N;
     for (uint32_t c = 0; c < n_contracts; ++c) {
@@ -374,7 +509,7 @@ int orc_mc_sums(const orc_params *p, const orc_contract *contracts, uint32_t n_c
             uint64_t hi = lo + ORC_CHUNK < n_paths ? lo + ORC_CHUNK : n_paths;
             for (uint64_t i = lo; i < hi; ++i) {
                 orc_path_normals(seed, path_begin + i, N, 0u, Za, Zb);
-                orc_milstein_path(p, T, N, M, trunc, Za, Zb, &w, NULL, NULL);
+                orc_scheme_path(p, T, N, M, trunc, scheme, Za, Zb, &w, NULL, NULL);
                 for (uint32_t c = 0; c < n_contracts; ++c) {
                     orc_estimators(p, &contracts[c], N, &w, est);
                     for (int e = 0; e < 6; ++e) {
@@ -401,9 +536,9 @@ int orc_mc_sums(const orc_params *p, const orc_contract *contracts, uint32_t n_c
  * the orc_path record and est[i*6*n_contracts ...] the estimators. */
 int orc_debug_paths(const orc_params *p, const orc_contract *contracts, uint32_t n_contracts,
                     const uint64_t *paths, uint64_t count, uint32_t N, uint64_t seed, int trunc,
-                    double *rec, double *est)
+                    int scheme, double *rec, double *est)
 {
-    if (n_contracts == 0 || N == 0) return -1;
+    if (n_contracts == 0 || N == 0 || !orc_scheme_ok(p, trunc, scheme)) return -1;
     const double T = contracts[0].T;
     uint32_t M = N;
     for (uint32_t c = 0; c < n_contracts; ++c) {
@@ -419,7 +554,7 @@ int orc_debug_paths(const orc_params *p, const orc_contract *contracts, uint32_t
     for (uint64_t i = 0; i < count; ++i) {
         orc_path w;
         orc_path_normals(seed, paths[i], N, 0u, Za, Zb);
-        orc_milstein_path(p, T, N, M, trunc, Za, Zb, &w, NULL, NULL);
+        orc_scheme_path(p, T, N, M, trunc, scheme, Za, Zb, &w, NULL, NULL);
         memcpy(rec + i * ORC_PATH_DOUBLES, &w, sizeof(double) * ORC_PATH_DOUBLES);
         for (uint32_t c = 0; c < n_contracts; ++c)
             orc_estimators(p, &contracts[c], N, &w, est + (i * n_contracts + c) * 6);
@@ -431,16 +566,16 @@ int orc_debug_paths(const orc_params *p, const orc_contract *contracts, uint32_t
 
 /* Single path from caller-supplied normals, with the full trajectory. */
 int orc_path_from_normals(const orc_params *p, const orc_contract *contracts, uint32_t n_contracts,
-                          uint32_t N, int trunc, const double *Za, const double *Zb,
+                          uint32_t N, int trunc, int scheme, const double *Za, const double *Zb,
                           double *rec, double *est, double *traj_X, double *traj_V)
 {
-    if (n_contracts == 0 || N == 0) return -1;
+    if (n_contracts == 0 || N == 0 || !orc_scheme_ok(p, trunc, scheme)) return -1;
     uint32_t M = N;
     for (uint32_t c = 0; c < n_contracts; ++c)
         if (contracts[c].payoff == 1 && contracts[c].n_monitor) M = contracts[c].n_monitor;
     if (N % M != 0) return -1;
     orc_path w;
-    orc_milstein_path(p, contracts[0].T, N, M, trunc, Za, Zb, &w, traj_X, traj_V);
+    orc_scheme_path(p, contracts[0].T, N, M, trunc, scheme, Za, Zb, &w, traj_X, traj_V);
     memcpy(rec, &w, sizeof(double) * ORC_PATH_DOUBLES);
     for (uint32_t c = 0; c < n_contracts; ++c)
         orc_estimators(p, &contracts[c], N, &w, est + c * 6);
@@ -450,10 +585,10 @@ int orc_path_from_normals(const orc_params *p, const orc_contract *contracts, ui
 /* Many paths from caller-supplied normals: Za, Zb are (n_paths x N) row-major;
  * rec receives n_paths x ORC_PATH_DOUBLES and est n_paths x n_contracts x 6. */
 int orc_paths_from_normals(const orc_params *p, const orc_contract *contracts, uint32_t n_contracts,
-                           uint32_t N, int trunc, uint64_t n_paths, const double *Za,
+                           uint32_t N, int trunc, int scheme, uint64_t n_paths, const double *Za,
                            const double *Zb, double *rec, double *est)
 {
-    if (n_contracts == 0 || N == 0) return -1;
+    if (n_contracts == 0 || N == 0 || !orc_scheme_ok(p, trunc, scheme)) return -1;
     uint32_t M = N;
     for (uint32_t c = 0; c < n_contracts; ++c) {
         if (contracts[c].T != contracts[0].T) return -1;
@@ -465,8 +600,8 @@ int orc_paths_from_normals(const orc_params *p, const orc_contract *contracts, u
 #endif
     for (int64_t i = 0; i < (int64_t)n_paths; ++i) {
         orc_path w;
-        orc_milstein_path(p, contracts[0].T, N, M, trunc, Za + (size_t)i * N, Zb + (size_t)i * N,
-                          &w, NULL, NULL);
+        orc_scheme_path(p, contracts[0].T, N, M, trunc, scheme, Za + (size_t)i * N,
+                        Zb + (size_t)i * N, &w, NULL, NULL);
         memcpy(rec + (size_t)i * ORC_PATH_DOUBLES, &w, sizeof(double) * ORC_PATH_DOUBLES);
         for (uint32_t c = 0; c < n_contracts; ++c)
             orc_estimators(p, &contracts[c], N, &w, est + ((size_t)i * n_contracts + c) * 6);
