@@ -321,6 +321,36 @@ def run_gpu(args):
                "path_steps_per_s_at_philox_se": n * w.n_steps / (q_ms * 1e-3) / se_ratio**2,
                "gpu_launches_per_step": 4}
 
+    # scheme variants on the same workload and launch: Euler (Sec. 2.4.1) and QE
+    schemes = None
+    if not args.no_schemes and world == 1:
+        schemes = {}
+        for sname, sid in (("euler", nv.HESTON_SCHEME_EULER), ("qe", nv.HESTON_SCHEME_QE)):
+            sopts = nv.make_options(prec=nv.HESTON_FP32, stream=stream, device=local, scheme=sid)
+            sout = torch.empty(nc * 12, dtype=torch.float64, device=dev)
+
+            def sstep():
+                nv.heston_mc_launch(params, contracts, n, w.n_steps, w.seed, sopts, ws, ws_bytes, sout)
+
+            for _ in range(3):
+                sstep()
+            barrier()
+            s_steps = max(3, min(args.steps, 30))
+            sev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(s_steps)]
+            clocks.mark(True)
+            for i in range(s_steps):
+                flush.fill_(i & 0xFF)
+                sev[i][0].record(stream)
+                sstep()
+                sev[i][1].record(stream)
+            barrier()
+            clocks.mark(False)
+            s_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in sev)
+            sest = sout.view(nc, 12).cpu().numpy()
+            schemes[sname] = {"ms_per_step": s_ms, "path_steps_per_s": n * w.n_steps / (s_ms * 1e-3),
+                              "price_k100_euro": float(sest[1, 0]), "price_se_k100_euro": float(sest[1, 6]),
+                              "gpu_launches_per_step": 3}
+
     # batched form: 1024 uneven contracts in one persistent launch (captured in a
     # CUDA graph) against one launch per contract, same paths hence same SE
     batched = None
@@ -565,6 +595,8 @@ def run_gpu(args):
             line["adjoint_variant"] = adjoint
         if serving is not None:
             line["serving_variant"] = serving
+        if schemes is not None:
+            line["scheme_variants"] = schemes
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
         print(json.dumps(line), flush=True)
@@ -585,6 +617,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 1024-contract form")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint gradient")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--no-schemes", action="store_true", help="skip the Euler / QE variants")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="request arrivals per second")
     ap.add_argument("--serve-seconds", type=float, default=5.0)
     ap.add_argument("--serve-tiles-per-round", type=int, default=16384)

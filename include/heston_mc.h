@@ -85,6 +85,22 @@ typedef struct {
 typedef enum { HESTON_TRUNC_FULL = 0, HESTON_TRUNC_PAPER_FLOOR = 1 } heston_trunc;
 typedef enum { HESTON_RNG_PHILOX = 0, HESTON_RNG_SOBOL_BB = 1 } heston_rng;
 typedef enum { HESTON_FP32 = 0, HESTON_FP64 = 1 } heston_prec;
+/* Discretisation of one step (all on the same Philox normals Za, Zb):
+ * MILSTEIN (Sec. 2.4.2, default); EULER (Sec. 2.4.1: the Milstein step
+ * without the xi^2 dt (Z2^2 - 1) / 4 term, same truncation choices); QE,
+ * Andersen's quadratic-exponential scheme (the method Sec. 5 names as the
+ * next one to try; L. Andersen, J. Comput. Finance 11(3), 2008): the
+ * variance from its exact conditional mean and variance, matched by
+ * a (b + Za)^2 when psi = s^2/m^2 <= 1.5 and by a point mass at zero plus
+ * an exponential tail driven by Uv = Phi(Za) above; ln S from both
+ * variances with the independent normal Zb, gamma1 = gamma2 = 1/2, no
+ * martingale correction.  QE ignores trunc (its variance is never
+ * negative) and needs kappa, theta, xi > 0 (HESTON_ERR_INVALID_ARG
+ * otherwise).  EULER and QE run with rng = PHILOX on the single-set entry
+ * points (heston_mc_price_greeks[_ex], heston_mc_launch[_noalloc],
+ * heston_mc_launch_tiles, heston_mc_debug_paths); the QMC, batched,
+ * serving and adjoint entry points return HESTON_ERR_UNSUPPORTED for them. */
+typedef enum { HESTON_SCHEME_MILSTEIN = 0, HESTON_SCHEME_EULER = 1, HESTON_SCHEME_QE = 2 } heston_scheme;
 
 /* Options.  trunc: full truncation (the state keeps its sign; drift,
  * diffusion and the Milstein term see max(V, 0)) or the paper's floor
@@ -104,6 +120,7 @@ typedef struct {
     int32_t device;
     uint32_t grid_ctas;
     uint32_t block_threads;
+    int32_t scheme;            /* heston_scheme */
     uint32_t reserved;
 } heston_options;
 

@@ -139,6 +139,13 @@ struct Coef {
     R xi, c4, c4T;                // c4 = xi^2 dt / 4, c4T = xi^2 / (4N)
     R rho, sq;                    // sq = sqrt(1 - rho^2)
     R kappa, theta;               // for the adjoint
+    // QE (E = e^{-kappa dt}, g = (1 - E)/kappa; *_T = d/dT at fixed N):
+    // m = qmth + V qE, s^2 = qs0 + V qs1, ln S += qK0r + qK1 V + qK2 V' + sq ut Zb
+    // with ut^2 = qhdt (V + V').
+    R qE, qE_T, qmth, qmth_T;
+    R qs1, qs1_T, qs0, qs0_T;
+    R qK0r, qK0r_T, qK1, qK2, qK12_T;
+    R qhdt, qhddt;
 };
 
 // Contracts priced on the shared paths (all with the same T and Asian M),
@@ -189,9 +196,11 @@ __device__ __forceinline__ void init_state(PathState<R> &s, R v0)
     s.GE = R(0); s.QE = R(0); s.GA = R(0); s.QA = R(0);
 }
 
-// One Milstein step with its tangents, from independent normals (za, zb).
+// One Milstein step with its tangents, from independent normals (za, zb);
+// EULER drops the xi^2 dt (Z2^2 - 1) / 4 term (Sec. 2.4.1).
 // FP32 full truncation: the same recursion with shared products hoisted
 // (xi Z2 feeds V and both V tangents; the truncation mask scales 1/(2u)).
+template <bool EULER>
 __device__ __forceinline__ void milstein_step_f32_full(PathState<float> &s, float za, float zb,
                                                        const Coef<float> &k)
 {
@@ -215,13 +224,13 @@ __device__ __forceinline__ void milstein_step_f32_full(PathState<float> &s, floa
     s.Xv = fmaf(uv, za, fmaf(-k.half_dt, Vpv, s.Xv));
     s.XT = fmaf(uT, za, fmaf(-k.half_dt, VpT, fmaf(drift, k.ddt, s.XT)));
     const float z2m1 = fmaf(Z2, Z2, -1.0f);
-    const float c4 = pos ? k.c4 : 0.0f, c4T = pos ? k.c4T : 0.0f;
+    const float c4 = (pos && !EULER) ? k.c4 : 0.0f, c4T = (pos && !EULER) ? k.c4T : 0.0f;
     s.V = fmaf(c4, z2m1, fmaf(xZ2, u, fmaf(-k.kdt, Vp, s.V + k.kth_dt)));
     s.Vv = fmaf(xZ2, uv, fmaf(-k.kdt, Vpv, s.Vv));
     s.VT = fmaf(c4T, z2m1, fmaf(xZ2, uT, fmaf(-k.kdt, VpT, fmaf(-k.kappa_ddt, Vp, s.VT + k.kth_ddt))));
 }
 
-template <typename R, int TRUNC>
+template <typename R, int TRUNC, bool EULER>
 __device__ __forceinline__ void milstein_step_generic(PathState<R> &s, R za, R zb, const Coef<R> &k)
 {
     const R Z1 = za;
@@ -248,7 +257,7 @@ __device__ __forceinline__ void milstein_step_generic(PathState<R> &s, R za, R z
     s.Xv += uv * Z1 - k.half_dt * Vpv;
     s.XT += drift * k.ddt - k.half_dt * VpT + uT * Z1;
 
-    const R z2m1 = Z2 * Z2 - R(1);
+    const R z2m1 = EULER ? R(0) : Z2 * Z2 - R(1);
     if (TRUNC == HESTON_TRUNC_FULL) {
         const R mil = pos ? k.c4 * z2m1 : R(0);
         const R milT = pos ? k.c4T * z2m1 : R(0);
@@ -267,13 +276,88 @@ __device__ __forceinline__ void milstein_step_generic(PathState<R> &s, R za, R z
     }
 }
 
-template <typename R, int TRUNC>
-__device__ __forceinline__ void milstein_step(PathState<R> &s, R za, R zb, const Coef<R> &k)
+__device__ __forceinline__ float norm_cdf(float x) { return normcdff(x); }
+__device__ __forceinline__ double norm_cdf(double x) { return normcdf(x); }
+__device__ __forceinline__ float log_pos(float x) { return lg2_approx(x) * 0.69314718f; }
+__device__ __forceinline__ double log_pos(double x) { return log(x); }
+
+// One QE step (Andersen 2008) with its tangents.  The variance: exact
+// conditional mean m and variance s^2 of the CIR transition, psi = s^2/m^2;
+// psi <= 1.5: V' = a (b + Za)^2, b^2 = 2/psi - 1 + sqrt(2/psi (2/psi - 1)),
+// a = m / (1 + b^2); psi > 1.5: V' = 0 when Phi(-Za) >= 1 - p, else
+// m ln((1 - p)/Phi(-Za)) / (1 - p) with 1 - p = 2 / (psi + 1).  Then
+// ln S' = ln S + r dt + K0 + K1 V + K2 V' + sq ut Zb, ut = sqrt(dt (V + V')/2);
+// Zb does not move the variance, so the Gamma weights are ut Zb and ut^2.
+template <typename R>
+__device__ __forceinline__ void qe_step(PathState<R> &s, R za, R zb, const Coef<R> &k)
 {
-    if constexpr (sizeof(R) == 4 && TRUNC == HESTON_TRUNC_FULL)
-        milstein_step_f32_full(s, za, zb, k);
+    const R m = k.qmth + s.V * k.qE;
+    const R mv = s.Vv * k.qE;
+    const R mT = k.qmth_T + s.V * k.qE_T + s.VT * k.qE;
+    const R s2 = k.qs0 + s.V * k.qs1;
+    const R s2v = s.Vv * k.qs1;
+    const R s2T = k.qs0_T + s.V * k.qs1_T + s.VT * k.qs1;
+    const R im = R(1) / m;                           // m >= theta (1 - E) > 0
+    const R psi = s2 * im * im;
+    const R psiv = (s2v - R(2) * s2 * mv * im) * im * im;
+    const R psiT = (s2T - R(2) * s2 * mT * im) * im * im;
+    R Vn, Vnv, VnT;
+    if (psi <= R(1.5)) {
+        const R y = R(2) / psi;
+        const R hy2 = R(-0.5) * y * y;               // dy/dpsi
+        const R root = sqrt(y * (y - R(1)));
+        const R b2 = y - R(1) + root;
+        const R db2 = (R(1) + (R(2) * y - R(1)) / (R(2) * root)) * hy2;   // db^2/dpsi
+        const R b = sqrt(b2);
+        const R ia = R(1) / (R(1) + b2);
+        const R a = m * ia;
+        const R b2v = db2 * psiv, b2T = db2 * psiT;
+        const R hb = R(0.5) / b;
+        const R av = (mv - a * b2v) * ia, aT = (mT - a * b2T) * ia;
+        const R bz = b + za;
+        Vn = a * bz * bz;
+        Vnv = bz * (av * bz + R(2) * a * b2v * hb);
+        VnT = bz * (aT * bz + R(2) * a * b2T * hb);
+    } else {
+        const R omp = R(2) / (psi + R(1));           // 1 - p
+        const R q = norm_cdf(-za);                   // 1 - Uv
+        if (q < omp) {
+            const R L = log_pos(omp / q);
+            const R iomp = R(1) / omp;
+            Vn = m * L * iomp;
+            Vnv = mv * L * iomp + R(0.5) * m * psiv * (L - R(1));
+            VnT = mT * L * iomp + R(0.5) * m * psiT * (L - R(1));
+        } else {
+            Vn = R(0); Vnv = R(0); VnT = R(0);
+        }
+    }
+    const R sum = s.V + Vn;
+    const R y = k.qhdt * sum;                        // ut^2
+    const R rs = rsqrt_pos(y);
+    const R ut = y * rs;
+    const R utv = R(0.5) * k.qhdt * (s.Vv + Vnv) * rs;
+    const R utT = R(0.5) * (k.qhddt * sum + k.qhdt * (s.VT + VnT)) * rs;
+    s.GE += ut * zb;
+    s.QE += y;
+    s.X += k.qK0r + k.qK1 * s.V + k.qK2 * Vn + k.sq * ut * zb;
+    s.Xv += k.qK1 * s.Vv + k.qK2 * Vnv + k.sq * utv * zb;
+    s.XT += k.qK0r_T + k.qK12_T * sum + k.qK1 * s.VT + k.qK2 * VnT + k.sq * utT * zb;
+    s.V = Vn; s.Vv = Vnv; s.VT = VnT;
+}
+
+// Scheme of a kernel instantiation: Milstein or Euler with full truncation
+// or the floor, or QE.  Values 0 and 1 are the Milstein truncations.
+enum { STEP_MIL_FULL = 0, STEP_MIL_FLOOR = 1, STEP_EUL_FULL = 2, STEP_EUL_FLOOR = 3, STEP_QE = 4 };
+
+template <typename R, int STEP>
+__device__ __forceinline__ void scheme_step(PathState<R> &s, R za, R zb, const Coef<R> &k)
+{
+    if constexpr (STEP == STEP_QE)
+        qe_step(s, za, zb, k);
+    else if constexpr (sizeof(R) == 4 && (STEP & 1) == HESTON_TRUNC_FULL)
+        milstein_step_f32_full<(STEP >= STEP_EUL_FULL)>(s, za, zb, k);
     else
-        milstein_step_generic<R, TRUNC>(s, za, zb, k);
+        milstein_step_generic<R, STEP & 1, (STEP >= STEP_EUL_FULL)>(s, za, zb, k);
 }
 
 // Asian monitoring date (first: the first date, which closes the Asian
@@ -345,7 +429,7 @@ enum { MON_NONE = 0, MON_EVERY = 1, MON_STRIDE = 2 };
 
 // Run NP paths (one lane) through all N steps.  Step k uses Philox counter
 // (k/2, path_lo, path_hi, 0): words (x, y) for even k, (z, w) for odd k.
-template <typename R, int TRUNC, int MON, int NP>
+template <typename R, int STEP, int MON, int NP>
 __device__ __forceinline__ void simulate(PathState<R> (&s)[NP], const uint32_t (&plo)[NP],
                                          const uint32_t (&phi)[NP], const Coef<R> &k,
                                          const ContractSet<R> &cs, PhiloxKey key, uint32_t N)
@@ -366,7 +450,7 @@ __device__ __forceinline__ void simulate(PathState<R> (&s)[NP], const uint32_t (
                 R za, zb;
                 if (h == 0) box_muller(w[q].x, w[q].y, za, zb);
                 else        box_muller(w[q].z, w[q].w, za, zb);
-                milstein_step<R, TRUNC>(s[q], za, zb, k);
+                scheme_step<R, STEP>(s[q], za, zb, k);
             }
             const uint32_t kp1 = 2u * j + 1u + (uint32_t)h;
             if (MON == MON_EVERY) {
@@ -388,7 +472,7 @@ __device__ __forceinline__ void simulate(PathState<R> (&s)[NP], const uint32_t (
             const uint4 w = philox4x32_10(make_uint4(n_pairs, plo[q], phi[q], 0u), key);
             R za, zb;
             box_muller(w.x, w.y, za, zb);
-            milstein_step<R, TRUNC>(s[q], za, zb, k);
+            scheme_step<R, STEP>(s[q], za, zb, k);
         }
         if (MON == MON_EVERY || (MON == MON_STRIDE && N == next_mon)) {
 #pragma unroll
@@ -403,7 +487,7 @@ __device__ __forceinline__ void simulate(PathState<R> (&s)[NP], const uint32_t (
 // sum_x and sum_x^2 (the lane's two paths added first, then a fixed xor
 // butterfly), so tile rows do not depend on the launch shape.
 // ---------------------------------------------------------------------------
-template <typename R, int TRUNC, int MON>
+template <typename R, int STEP, int MON>
 __global__ void __launch_bounds__(kPathBlock) heston_paths_kernel(Coef<R> k, ContractSet<R> cs, Launch a)
 {
     const int lane = threadIdx.x & 31;
@@ -424,7 +508,7 @@ __global__ void __launch_bounds__(kPathBlock) heston_paths_kernel(Coef<R> k, Con
             plo[q] = (uint32_t)g;
             phi[q] = (uint32_t)(g >> 32);
         }
-        simulate<R, TRUNC, MON, 2>(s, plo, phi, k, cs, a.key, a.N);
+        simulate<R, STEP, MON, 2>(s, plo, phi, k, cs, a.key, a.N);
 
         R eT[2];
 #pragma unroll
@@ -474,7 +558,7 @@ __device__ void write_debug_record(const PathState<R> &s, const ContractSet<R> &
 
 // Test kernel: one thread per requested path, the same step code, writes the
 // per-path record and estimators.
-template <typename R, int TRUNC, int MON>
+template <typename R, int STEP, int MON>
 __global__ void heston_debug_kernel(Coef<R> k, ContractSet<R> cs, PhiloxKey key, uint32_t N,
                                     const uint64_t *paths, uint32_t count, double *rec, double *est)
 {
@@ -483,7 +567,7 @@ __global__ void heston_debug_kernel(Coef<R> k, ContractSet<R> cs, PhiloxKey key,
     const uint64_t g = paths[i];
     PathState<R> s[1];
     const uint32_t plo[1] = {(uint32_t)g}, phi[1] = {(uint32_t)(g >> 32)};
-    simulate<R, TRUNC, MON, 1>(s, plo, phi, k, cs, key, N);
+    simulate<R, STEP, MON, 1>(s, plo, phi, k, cs, key, N);
     write_debug_record(s[0], cs, rec + (uint64_t)i * kRecordDoubles, est + (uint64_t)i * cs.n * 6);
 }
 
@@ -620,7 +704,7 @@ __device__ __forceinline__ void simulate_qmc(PathState<float> (&s)[NP], const ui
         }
         --top;
 #pragma unroll
-        for (int q = 0; q < NP; ++q) milstein_step<float, TRUNC>(s[q], za[q], zb[q], k);
+        for (int q = 0; q < NP; ++q) scheme_step<float, TRUNC>(s[q], za[q], zb[q], k);
         const uint32_t kp1 = kk + 1u;
         if (MON == MON_EVERY) {
 #pragma unroll
@@ -1149,7 +1233,7 @@ struct Prepared {
     ContractSet<double> cs;
     ContractSet<float> csf;
     Coef<float> kf;
-    Coef<double> kd;
+    Coef<double> kd{};
     heston_options opt;
     uint32_t N;
     bool gamma_nan;
@@ -1160,6 +1244,20 @@ template <> const ContractSet<double> &cs_of<double>(const Prepared &pp) { retur
 template <> const ContractSet<float> &cs_of<float>(const Prepared &pp) { return pp.csf; }
 
 bool finite_nonneg(double x) { return std::isfinite(x) && x >= 0.0; }
+
+// Every coefficient rounded once from its FP64 value.
+template <typename D>
+Coef<D> coef_cast(const Coef<double> &k)
+{
+    static_assert(sizeof(Coef<double>) % sizeof(double) == 0, "Coef holds doubles only");
+    constexpr int n = (int)(sizeof(Coef<double>) / sizeof(double));
+    static_assert(sizeof(Coef<D>) == n * sizeof(D), "Coef layout");
+    const double *src = reinterpret_cast<const double *>(&k);
+    Coef<D> out;
+    D *dst = reinterpret_cast<D *>(&out);
+    for (int i = 0; i < n; ++i) dst[i] = (D)src[i];
+    return out;
+}
 
 int validate_and_prepare(const heston_params *p, const heston_contract *c, uint32_t nc,
                          uint64_t n_paths, uint32_t N, const heston_options *opts, Prepared &out)
@@ -1184,6 +1282,11 @@ int validate_and_prepare(const heston_params *p, const heston_contract *c, uint3
     if (o.prec != HESTON_FP32 && o.prec != HESTON_FP64) return HESTON_ERR_INVALID_ARG;
     if (o.rng != HESTON_RNG_PHILOX && o.rng != HESTON_RNG_SOBOL_BB) return HESTON_ERR_INVALID_ARG;
     if (o.reserved != 0) return HESTON_ERR_INVALID_ARG;
+    if (o.scheme != HESTON_SCHEME_MILSTEIN && o.scheme != HESTON_SCHEME_EULER && o.scheme != HESTON_SCHEME_QE)
+        return HESTON_ERR_INVALID_ARG;
+    if (o.scheme == HESTON_SCHEME_QE && !(p->kappa > 0.0 && p->theta > 0.0 && p->xi > 0.0))
+        return HESTON_ERR_INVALID_ARG;
+    if (o.scheme != HESTON_SCHEME_MILSTEIN && o.rng != HESTON_RNG_PHILOX) return HESTON_ERR_UNSUPPORTED;
     if (o.block_threads != 0 && (o.block_threads % 32 != 0 || o.block_threads > kPathBlock))
         return HESTON_ERR_INVALID_ARG;
 
@@ -1255,13 +1358,30 @@ int validate_and_prepare(const heston_params *p, const heston_contract *c, uint3
     kd.sq = sq;
     kd.kappa = p->kappa;
     kd.theta = p->theta;
-    Coef<float> kf;
-    kf.v0 = (float)kd.v0; kf.dt = (float)kd.dt; kf.ddt = (float)kd.ddt;
-    kf.half_dt = (float)kd.half_dt; kf.r = (float)kd.r; kf.kdt = (float)kd.kdt;
-    kf.kth_dt = (float)kd.kth_dt; kf.kth_ddt = (float)kd.kth_ddt; kf.kappa_ddt = (float)kd.kappa_ddt;
-    kf.xi = (float)kd.xi; kf.c4 = (float)kd.c4; kf.c4T = (float)kd.c4T;
-    kf.rho = (float)kd.rho; kf.sq = (float)kd.sq;
-    kf.kappa = (float)kd.kappa; kf.theta = (float)kd.theta;
+    // QE constants (zero unless the scheme is QE, which has kappa, theta, xi > 0)
+    if (o.scheme == HESTON_SCHEME_QE) {
+        const double kap = p->kappa, th = p->theta, xi2 = p->xi * p->xi;
+        const double E = std::exp(-kap * dt), omE = -std::expm1(-kap * dt);
+        const double E_T = -kap * E * ddt;                  // dE/dT
+        const double g = omE / kap, g_T = E * ddt;          // (1 - E)/kappa and d/dT
+        kd.qE = E;
+        kd.qE_T = E_T;
+        kd.qmth = th * omE;
+        kd.qmth_T = -th * E_T;
+        kd.qs1 = xi2 * E * g;
+        kd.qs1_T = xi2 * (E_T * g + E * g_T);
+        kd.qs0 = 0.5 * th * xi2 * omE * g;
+        kd.qs0_T = 0.5 * th * xi2 * (-E_T * g + omE * g_T);
+        const double kr = kap * p->rho / p->xi - 0.5;
+        kd.qK0r = p->r * dt - p->rho * kap * th * dt / p->xi;
+        kd.qK0r_T = p->r * ddt - p->rho * kap * th * ddt / p->xi;
+        kd.qK1 = 0.5 * dt * kr - p->rho / p->xi;
+        kd.qK2 = 0.5 * dt * kr + p->rho / p->xi;
+        kd.qK12_T = 0.5 * ddt * kr;
+        kd.qhdt = 0.5 * dt;
+        kd.qhddt = 0.5 * ddt;
+    }
+    const Coef<float> kf = coef_cast<float>(kd);
 
     out.cs = cs;
     out.csf = csf;
@@ -1284,10 +1404,10 @@ size_t workspace_bytes(uint32_t nc, uint64_t n_paths)
     return align256(nt * w) + align256(groups_for(nt) * w);
 }
 
-template <typename R, int TRUNC, int MON>
+template <typename R, int STEP, int MON>
 cudaError_t launch_paths_t(const Prepared &pp, const Coef<R> &k, const Launch &a, cudaStream_t st)
 {
-    auto kern = heston_paths_kernel<R, TRUNC, MON>;
+    auto kern = heston_paths_kernel<R, STEP, MON>;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -1319,18 +1439,32 @@ int mon_mode(const ContractSet<double> &cs)
     return cs.stride == 1 ? MON_EVERY : MON_STRIDE;
 }
 
+// Kernel instantiation of the options' scheme and truncation.
+int step_of(const heston_options &o)
+{
+    if (o.scheme == HESTON_SCHEME_QE) return STEP_QE;
+    return (o.scheme == HESTON_SCHEME_EULER ? STEP_EUL_FULL : STEP_MIL_FULL) + (o.trunc & 1);
+}
+
+template <typename R, int STEP>
+cudaError_t launch_paths_s(const Prepared &pp, const Coef<R> &k, const Launch &a, cudaStream_t st)
+{
+    const int mon = mon_mode(pp.cs);
+    if (mon == MON_NONE) return launch_paths_t<R, STEP, MON_NONE>(pp, k, a, st);
+    if (mon == MON_EVERY) return launch_paths_t<R, STEP, MON_EVERY>(pp, k, a, st);
+    return launch_paths_t<R, STEP, MON_STRIDE>(pp, k, a, st);
+}
+
 template <typename R>
 cudaError_t launch_paths_r(const Prepared &pp, const Coef<R> &k, const Launch &a, cudaStream_t st)
 {
-    const int mon = mon_mode(pp.cs);
-    if (pp.opt.trunc == HESTON_TRUNC_FULL) {
-        if (mon == MON_NONE) return launch_paths_t<R, 0, MON_NONE>(pp, k, a, st);
-        if (mon == MON_EVERY) return launch_paths_t<R, 0, MON_EVERY>(pp, k, a, st);
-        return launch_paths_t<R, 0, MON_STRIDE>(pp, k, a, st);
+    switch (step_of(pp.opt)) {
+    case STEP_MIL_FULL: return launch_paths_s<R, STEP_MIL_FULL>(pp, k, a, st);
+    case STEP_MIL_FLOOR: return launch_paths_s<R, STEP_MIL_FLOOR>(pp, k, a, st);
+    case STEP_EUL_FULL: return launch_paths_s<R, STEP_EUL_FULL>(pp, k, a, st);
+    case STEP_EUL_FLOOR: return launch_paths_s<R, STEP_EUL_FLOOR>(pp, k, a, st);
+    default: return launch_paths_s<R, STEP_QE>(pp, k, a, st);
     }
-    if (mon == MON_NONE) return launch_paths_t<R, 1, MON_NONE>(pp, k, a, st);
-    if (mon == MON_EVERY) return launch_paths_t<R, 1, MON_EVERY>(pp, k, a, st);
-    return launch_paths_t<R, 1, MON_STRIDE>(pp, k, a, st);
 }
 
 cudaError_t launch_paths(const Prepared &pp, const Launch &a, cudaStream_t st)
@@ -1760,7 +1894,8 @@ int batch_prepare_items(const heston_batch_item *items, uint32_t n, const heston
     if (!items || n == 0 || !plan) return HESTON_ERR_INVALID_ARG;
     heston_options o;
     if (opts) o = *opts; else { std::memset(&o, 0, sizeof(o)); o.device = -1; }
-    if (o.prec != HESTON_FP32 || o.rng != HESTON_RNG_PHILOX) return HESTON_ERR_UNSUPPORTED;
+    if (o.prec != HESTON_FP32 || o.rng != HESTON_RNG_PHILOX || o.scheme != HESTON_SCHEME_MILSTEIN)
+        return HESTON_ERR_UNSUPPORTED;
     uint64_t tiles = 0, groups = 0, ps = 0;
     if (dev) dev->resize(n);
     for (uint32_t i = 0; i < n; ++i) {
@@ -1937,7 +2072,8 @@ int adjoint_enqueue(bool backward, const heston_params *params, const heston_con
     Prepared pp;
     int rc = validate_and_prepare(params, contract, 1, n_paths, N, opts, pp);
     if (rc < 0) return rc;
-    if (pp.opt.prec != HESTON_FP32 || pp.opt.trunc != HESTON_TRUNC_FULL || pp.opt.rng != HESTON_RNG_PHILOX)
+    if (pp.opt.prec != HESTON_FP32 || pp.opt.trunc != HESTON_TRUNC_FULL || pp.opt.rng != HESTON_RNG_PHILOX ||
+        pp.opt.scheme != HESTON_SCHEME_MILSTEIN)
         return HESTON_ERR_UNSUPPORTED;
     const AdjLayout L = adj_layout(n_paths, N);
     if (L.C > (uint32_t)kAdjMaxSeg) return HESTON_ERR_UNSUPPORTED;
@@ -2480,16 +2616,20 @@ int heston_mc_debug_paths(const heston_params *params, const heston_contract *co
         const unsigned grid = (count + 127) / 128;
         const PhiloxKey key = key_of(rng_seed);
         const int mon = mon_mode(pp.cs);
-        const bool full = pp.opt.trunc == HESTON_TRUNC_FULL;
-#define HESTON_DBG(R, TR, MO, K) heston_debug_kernel<R, TR, MO><<<grid, 128, 0, st>>>(K, cs_of<R>(pp), key, pp.N, dp, count, dr, de)
-#define HESTON_DBG_M(R, TR, K) do { if (mon == MON_NONE) HESTON_DBG(R, TR, MON_NONE, K); \
-                                    else if (mon == MON_EVERY) HESTON_DBG(R, TR, MON_EVERY, K); \
-                                    else HESTON_DBG(R, TR, MON_STRIDE, K); } while (0)
-        if (pp.opt.prec == HESTON_FP32) {
-            if (full) HESTON_DBG_M(float, 0, pp.kf); else HESTON_DBG_M(float, 1, pp.kf);
-        } else {
-            if (full) HESTON_DBG_M(double, 0, pp.kd); else HESTON_DBG_M(double, 1, pp.kd);
-        }
+        const int step = step_of(pp.opt);
+#define HESTON_DBG(R, SP, MO, K) heston_debug_kernel<R, SP, MO><<<grid, 128, 0, st>>>(K, cs_of<R>(pp), key, pp.N, dp, count, dr, de)
+#define HESTON_DBG_M(R, SP, K) do { if (mon == MON_NONE) HESTON_DBG(R, SP, MON_NONE, K); \
+                                    else if (mon == MON_EVERY) HESTON_DBG(R, SP, MON_EVERY, K); \
+                                    else HESTON_DBG(R, SP, MON_STRIDE, K); } while (0)
+#define HESTON_DBG_S(R, K) do { switch (step) { \
+            case STEP_MIL_FULL: HESTON_DBG_M(R, STEP_MIL_FULL, K); break; \
+            case STEP_MIL_FLOOR: HESTON_DBG_M(R, STEP_MIL_FLOOR, K); break; \
+            case STEP_EUL_FULL: HESTON_DBG_M(R, STEP_EUL_FULL, K); break; \
+            case STEP_EUL_FLOOR: HESTON_DBG_M(R, STEP_EUL_FLOOR, K); break; \
+            default: HESTON_DBG_M(R, STEP_QE, K); } } while (0)
+        if (pp.opt.prec == HESTON_FP32) HESTON_DBG_S(float, pp.kf);
+        else HESTON_DBG_S(double, pp.kd);
+#undef HESTON_DBG_S
 #undef HESTON_DBG_M
 #undef HESTON_DBG
         if (cudaGetLastError() != cudaSuccess) e = HESTON_ERR_CUDA;

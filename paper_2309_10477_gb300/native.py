@@ -34,6 +34,7 @@ HESTON_EUROPEAN, HESTON_ASIAN_ARITH = 0, 1
 HESTON_TRUNC_FULL, HESTON_TRUNC_PAPER_FLOOR = 0, 1
 HESTON_RNG_PHILOX, HESTON_RNG_SOBOL_BB = 0, 1
 HESTON_FP32, HESTON_FP64 = 0, 1
+HESTON_SCHEME_MILSTEIN, HESTON_SCHEME_EULER, HESTON_SCHEME_QE = 0, 1, 2
 
 ESTIMATORS = ("price", "delta", "gamma", "vega", "rho", "theta")
 RECORD_FIELDS = ("X", "V", "X_v", "V_v", "X_T", "V_T", "sumS", "sumtS", "sumS_Xv", "sumS_XT",
@@ -54,7 +55,8 @@ class heston_options(ctypes.Structure):
     _fields_ = [("trunc", ctypes.c_int32), ("rng", ctypes.c_int32), ("prec", ctypes.c_int32),
                 ("n_shifts", ctypes.c_uint32), ("cuda_stream", ctypes.c_void_p),
                 ("device", ctypes.c_int32), ("grid_ctas", ctypes.c_uint32),
-                ("block_threads", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("block_threads", ctypes.c_uint32), ("scheme", ctypes.c_int32),
+                ("reserved", ctypes.c_uint32)]
 
 
 class heston_result(ctypes.Structure):
@@ -195,9 +197,10 @@ def make_contract(payoff, K, T, is_put=0, n_monitor=0) -> heston_contract:
 
 
 def make_options(trunc=HESTON_TRUNC_FULL, prec=HESTON_FP64, stream=None, device=-1, grid_ctas=0,
-                 block_threads=0, rng=HESTON_RNG_PHILOX, n_shifts=0) -> heston_options:
+                 block_threads=0, rng=HESTON_RNG_PHILOX, n_shifts=0,
+                 scheme=HESTON_SCHEME_MILSTEIN) -> heston_options:
     return heston_options(trunc, rng, prec, n_shifts, _ptr(stream) or None, device, grid_ctas,
-                          block_threads, 0)
+                          block_threads, scheme, 0)
 
 
 def _contract_array(contracts):
