@@ -43,7 +43,7 @@ ALGO_INSTR_PER_PATH_STEP = 98
 ISSUE_LANES_PER_SM_CLK = 128          # 4 SM sub-partitions x 1 warp-instruction x 32 lanes
 FLUSH_BYTES = 256 << 20               # > 129 MB L2
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "heston_paths_kernel_multi_strike_2p22.md")
-KERNEL_SOURCE = os.path.join(ROOT, "paper_2309_10477_gb300", "csrc", "heston_mc.cu")
+KERNEL_SOURCE = os.path.join(ROOT, "paper_2309_10477_gb300", "csrc", "heston_device.cuh")
 
 
 def _dist_env():

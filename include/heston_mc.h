@@ -157,8 +157,9 @@ int heston_mc_price_greeks(const heston_params *params, const heston_contract *c
 /* Price n_contracts (1..HESTON_MAX_CONTRACTS) options on the same n_paths
  * paths of n_steps steps.  All contracts must share T; Asian contracts must
  * share M.  opts may be NULL (defaults).  out: host array of n_contracts.
- * Allocates its device workspace stream-ordered on opts->cuda_stream, and
- * returns after that stream has produced the results.
+ * Allocates its device workspace stream-ordered on opts->cuda_stream, from
+ * a pool that keeps the memory for the next call (heston_release_cached_memory
+ * returns it), and returns after that stream has produced the results.
  * HESTON_ERR_INVALID_ARG when: a pointer is NULL; S0 <= 0; K < 0; T <= 0;
  * v0, theta, kappa or xi < 0; |rho| > 1; any value not finite; n_steps == 0;
  * n_paths < 2 or > 2^40; N % M != 0; contracts disagree on T or on M;
@@ -369,6 +370,17 @@ int heston_mc_launch_batch(const heston_batch_plan *plan, const void *d_desc,
  * out: host array of n_items results. */
 int heston_mc_price_greeks_batch(const heston_batch_item *items, uint32_t n_items,
                                  const heston_options *opts, heston_result *out);
+
+/* ---- cached scratch -------------------------------------------------------- */
+
+/* The synchronous entry points (heston_mc_price_greeks[_ex] and
+ * heston_mc_debug_paths) take their device scratch stream-ordered from a
+ * memory pool per device owned by this library, which keeps freed blocks
+ * mapped for the next call.  This returns the unused cached memory of one
+ * device (device >= 0) or of every device (device = -1) to the driver;
+ * memory still in use by a call in flight stays.  HESTON_ERR_INVALID_ARG
+ * for device >= 64; HESTON_ERR_CUDA if the driver refuses. */
+int heston_release_cached_memory(int32_t device);
 
 /* ---- serving engine (continuous batching) ---------------------------------- */
 

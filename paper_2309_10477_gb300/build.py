@@ -8,7 +8,7 @@ import subprocess
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _ROOT = os.path.dirname(_HERE)
 SOURCES = [os.path.join(_HERE, "csrc", "heston_mc.cu")]
-HEADERS = [os.path.join(_ROOT, "include", "heston_mc.h")]
+HEADERS = [os.path.join(_ROOT, "include", "heston_mc.h"), os.path.join(_HERE, "csrc", "heston_device.cuh")]
 TARGET = os.path.join(_HERE, "libhestonmc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

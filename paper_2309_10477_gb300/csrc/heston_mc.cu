@@ -37,1175 +37,9 @@
 
 #include "heston_mc.h"
 
+#include "heston_device.cuh"
+
 namespace {
-
-constexpr int kTile = HESTON_TILE_PATHS;   // paths per tile = 32 lanes x 2
-constexpr int kMaxC = HESTON_MAX_CONTRACTS;
-constexpr int kGroupTiles = 256;           // tiles per first-level reduction group
-constexpr int kRecordDoubles = 15;
-constexpr int kPathBlock = 128;            // default threads per path-kernel CTA
-
-// ---------------------------------------------------------------------------
-// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
-// 32x32->64 multiplies, the high halves xored with the other two words and
-// the round key; the key advances by the Weyl constants between rounds.
-// ---------------------------------------------------------------------------
-struct PhiloxKey {
-    uint32_t k0, k1;
-};
-
-__host__ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, PhiloxKey key)
-{
-    uint32_t k0 = key.k0, k1 = key.k1;
-#pragma unroll
-    for (int i = 0; i < 10; ++i) {
-        const unsigned long long p0 = (unsigned long long)c.x * 0xD2511F53u;
-        const unsigned long long p1 = (unsigned long long)c.z * 0xCD9E8D57u;
-        const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
-        const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
-        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
-    }
-    return c;
-}
-
-// ---------------------------------------------------------------------------
-// Box-Muller on 24-bit uniforms: u1 = (a>>8 + 1) 2^-24 in (0,1],
-// u2 = (b>>8) 2^-24 in [0,1); Za = sqrt(-2 ln u1) cos 2 pi u2,
-// Zb = sqrt(-2 ln u1) sin 2 pi u2.  The uniforms are exact in both precisions.
-// ---------------------------------------------------------------------------
-// FP32 special-function unit approximations (PTX .approx forms).  Documented
-// bounds: sin/cos absolute error about 2^-20.9 on [-pi, pi]; lg2 absolute
-// error about 2^-22; ex2, rsqrt, sqrt relative error about 2^-22.
-__device__ __forceinline__ float sin_approx(float x) { float y; asm("sin.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x)); return y; }
-__device__ __forceinline__ float cos_approx(float x) { float y; asm("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x)); return y; }
-__device__ __forceinline__ float ex2_approx(float x) { float y; asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x)); return y; }
-__device__ __forceinline__ float sqrt_approx(float x) { float y; asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x)); return y; }
-__device__ __forceinline__ float lg2_approx(float x) { float y; asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x)); return y; }
-__device__ __forceinline__ float rsqrt_approx(float x) { float y; asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x)); return y; }
-
-__device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float &za, float &zb)
-{
-    // u1 = (a>>8) 2^-24 + 2^-24: the top 24 bits convert exactly.
-    const float u1 = fmaf((float)(a & 0xFFFFFF00u), 2.3283064365386963e-10f, 5.9604644775390625e-8f);
-    // The top 24 bits of b read as a signed 32-bit integer are 2^32 (u2 - [u2 >= 1/2]),
-    // so the angle 2 pi u2 lands in [-pi, pi) with the same sine and cosine.
-    const float ang = (float)(int32_t)(b & 0xFFFFFF00u) * 1.4629180792671596e-9f;   // 2 pi / 2^32
-    // r2 = -2 ln u1.  For u1 <= 0.9 from lg2.approx, whose absolute error
-    // (2 ln2 2^-22 in r2) is below 1.6e-6 of r2 >= 0.21.  Near 1, where that
-    // absolute error would swamp the small radius, from the series
-    // -2 ln(1 - w) = 2 sum_k w^k / k in w = 1 - u1 (exact), truncated after
-    // w^7 (relative error < 1.4e-8 at w = 0.1).  Both are evaluated and one
-    // selected: lanes of a warp fall on both sides.
-    const float w = 1.0f - u1;
-    const float r2_far = -1.3862943611198906f * lg2_approx(u1);
-    float p = fmaf(w, 0.2857142857f, 0.3333333333f);
-    p = fmaf(w, p, 0.4f);
-    p = fmaf(w, p, 0.5f);
-    p = fmaf(w, p, 0.6666666667f);
-    p = fmaf(w, p, 1.0f);
-    p = fmaf(w, p, 2.0f);
-    const float r2 = u1 > 0.9f ? w * p : r2_far;
-    const float rad = sqrt_approx(r2);
-    za = rad * cos_approx(ang);
-    zb = rad * sin_approx(ang);
-}
-
-__device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, double &za, double &zb)
-{
-    const double u1 = (double)((a >> 8) + 1u) * 5.9604644775390625e-8;
-    const double u2 = (double)(b >> 8) * 5.9604644775390625e-8;
-    const double rad = sqrt(-2.0 * log(u1));
-    double s, c;
-    sincospi(2.0 * u2, &s, &c);
-    za = rad * c;
-    zb = rad * s;
-}
-
-__device__ __forceinline__ float rsqrt_pos(float y) { return y > 0.0f ? rsqrt_approx(y) : 0.0f; }
-__device__ __forceinline__ double rsqrt_pos(double y) { return y > 0.0 ? rsqrt(y) : 0.0; }
-__device__ __forceinline__ float exp_r(float x) { return ex2_approx(x * 1.44269504f); }
-__device__ __forceinline__ double exp_r(double x) { return exp(x); }
-
-// ---------------------------------------------------------------------------
-// Scheme coefficients, computed in FP64 on the host and rounded once.
-// ---------------------------------------------------------------------------
-template <typename R>
-struct Coef {
-    R v0;
-    R dt, ddt, half_dt, r;        // dt = T/N, ddt = d(dt)/dT = 1/N
-    R kdt, kth_dt, kth_ddt, kappa_ddt;
-    R xi, c4, c4T;                // c4 = xi^2 dt / 4, c4T = xi^2 / (4N)
-    R rho, sq;                    // sq = sqrt(1 - rho^2)
-    R kappa, theta;               // for the adjoint
-    // QE (E = e^{-kappa dt}, g = (1 - E)/kappa; *_T = d/dT at fixed N):
-    // m = qmth + V qE, s^2 = qs0 + V qs1, ln S += qK0r + qK1 V + qK2 V' + sq ut Zb
-    // with ut^2 = qhdt (V + V').
-    R qE, qE_T, qmth, qmth_T;
-    R qs1, qs1_T, qs0, qs0_T;
-    R qK0r, qK0r_T, qK1, qK2, qK12_T;
-    R qhdt, qhddt;
-};
-
-// Contracts priced on the shared paths (all with the same T and Asian M),
-// with their constants rounded once on the host to the path precision.
-template <typename R>
-struct ContractSet {
-    int32_t n;
-    int32_t has_asian;
-    uint32_t M, stride;           // Asian dates and steps between them
-    int32_t payoff[kMaxC];
-    int32_t is_put[kMaxC];
-    R K[kMaxC];
-    R T, D, r;                    // D = exp(-rT)
-    R S0, inv_S0, inv_S0sq;
-    R inv_sq;                     // 1 / sqrt(1 - rho^2)
-    R S0_over_M;                  // S0 / M
-    R dAr_scale;                  // S0 T / M^2: d Sbar / dr = dAr_scale ((M+1) sA - sC)
-    R Mp1;                        // M + 1
-};
-
-struct Launch {
-    PhiloxKey key;
-    uint64_t path_begin;          // global index of local path 0
-    uint64_t n_paths;             // local paths
-    uint64_t n_tiles;
-    uint32_t N;
-    double *tile_sums;            // [n_tiles][12 * n]
-};
-
-// Registers of one path.  X = ln(S/S0); *_v = d/dv0, *_T = d/dT tangents.
-// Over the dates i = 1..M: sA = sum_i e^{X(t_i)} (running), sC = sum of the
-// running sA after each date, so that sum_i i e^{X(t_i)} = (M+1) sA - sC;
-// sAv / sAT = sum_i e^{X(t_i)} X_v(t_i) / X_T(t_i).  GE/QE: Gamma weights
-// sum_k u_k W_k and sum_k V_k+ dt over all steps; GA/QA: the same over the
-// steps before the first monitoring date.
-template <typename R>
-struct PathState {
-    R X, V, Xv, Vv, XT, VT;
-    R sA, sC, sAv, sAT;
-    R GE, QE, GA, QA;
-};
-
-template <typename R>
-__device__ __forceinline__ void init_state(PathState<R> &s, R v0)
-{
-    s.X = R(0); s.V = v0; s.Xv = R(0); s.Vv = R(1); s.XT = R(0); s.VT = R(0);
-    s.sA = R(0); s.sC = R(0); s.sAv = R(0); s.sAT = R(0);
-    s.GE = R(0); s.QE = R(0); s.GA = R(0); s.QA = R(0);
-}
-
-// One Milstein step with its tangents, from independent normals (za, zb);
-// EULER drops the xi^2 dt (Z2^2 - 1) / 4 term (Sec. 2.4.1).
-// FP32 full truncation: the same recursion with shared products hoisted
-// (xi Z2 feeds V and both V tangents; the truncation mask scales 1/(2u)).
-template <bool EULER>
-__device__ __forceinline__ void milstein_step_f32_full(PathState<float> &s, float za, float zb,
-                                                       const Coef<float> &k)
-{
-    const float Z2 = fmaf(k.rho, za, k.sq * zb);
-    const float W = fmaf(k.sq, za, -k.rho * zb);
-    const float xZ2 = k.xi * Z2;
-    const bool pos = s.V > 0.0f;
-    const float Vp = fmaxf(s.V, 0.0f);
-    const float Vpv = pos ? s.Vv : 0.0f;
-    const float VpT = pos ? s.VT : 0.0f;
-    const float y = Vp * k.dt;                                  // V+ dt
-    const float rs = rsqrt_approx(fmaxf(y, 1e-30f));            // finite at y = 0
-    const float u = y * rs;                                     // sqrt(V+ dt), 0 at 0
-    const float hdt = 0.5f * k.dt * rs;                         // dt / (2u)
-    const float uv = Vpv * hdt;                                 // du/dv0
-    const float uT = fmaf(VpT, hdt, Vp * (0.5f * k.ddt * rs));  // du/dT
-    s.GE = fmaf(u, W, s.GE);
-    s.QE += y;
-    const float drift = fmaf(-0.5f, Vp, k.r);
-    s.X = fmaf(u, za, fmaf(drift, k.dt, s.X));
-    s.Xv = fmaf(uv, za, fmaf(-k.half_dt, Vpv, s.Xv));
-    s.XT = fmaf(uT, za, fmaf(-k.half_dt, VpT, fmaf(drift, k.ddt, s.XT)));
-    const float z2m1 = fmaf(Z2, Z2, -1.0f);
-    const float c4 = (pos && !EULER) ? k.c4 : 0.0f, c4T = (pos && !EULER) ? k.c4T : 0.0f;
-    s.V = fmaf(c4, z2m1, fmaf(xZ2, u, fmaf(-k.kdt, Vp, s.V + k.kth_dt)));
-    s.Vv = fmaf(xZ2, uv, fmaf(-k.kdt, Vpv, s.Vv));
-    s.VT = fmaf(c4T, z2m1, fmaf(xZ2, uT, fmaf(-k.kdt, VpT, fmaf(-k.kappa_ddt, Vp, s.VT + k.kth_ddt))));
-}
-
-template <typename R, int TRUNC, bool EULER>
-__device__ __forceinline__ void milstein_step_generic(PathState<R> &s, R za, R zb, const Coef<R> &k)
-{
-    const R Z1 = za;
-    const R Z2 = k.rho * za + k.sq * zb;
-    const R W = k.sq * za - k.rho * zb;             // Z1 = rho Z2 + sq W
-
-    const bool pos = s.V > R(0);
-    const R Vp = pos ? s.V : R(0);
-    const R Vpv = pos ? s.Vv : R(0);
-    const R VpT = pos ? s.VT : R(0);
-    const R y = Vp * k.dt;                           // V+ dt
-    const R rs = rsqrt_pos(y);                       // 1 / sqrt(V+ dt), 0 at 0
-    const R u = y * rs;                              // sqrt(V+ dt)
-    const R hr = R(0.5) * rs;
-    const R uv = Vpv * k.dt * hr;                    // du/dv0
-    const R uT = (VpT * k.dt + Vp * k.ddt) * hr;     // du/dT
-
-    s.GE += u * W;
-    s.QE += y;
-
-    // ln S with the pre-update variance
-    const R drift = k.r - R(0.5) * Vp;
-    s.X += drift * k.dt + u * Z1;
-    s.Xv += uv * Z1 - k.half_dt * Vpv;
-    s.XT += drift * k.ddt - k.half_dt * VpT + uT * Z1;
-
-    const R z2m1 = EULER ? R(0) : Z2 * Z2 - R(1);
-    if (TRUNC == HESTON_TRUNC_FULL) {
-        const R mil = pos ? k.c4 * z2m1 : R(0);
-        const R milT = pos ? k.c4T * z2m1 : R(0);
-        s.V += k.kth_dt - k.kdt * Vp + k.xi * u * Z2 + mil;
-        s.Vv += k.xi * uv * Z2 - k.kdt * Vpv;
-        s.VT += k.kth_ddt - k.kappa_ddt * Vp - k.kdt * VpT + k.xi * uT * Z2 + milT;
-    } else {
-        const R Vt = s.V + k.kth_dt - k.kdt * s.V + k.xi * u * Z2 + k.c4 * z2m1;
-        const R Vtv = s.Vv - k.kdt * s.Vv + k.xi * uv * Z2;
-        const R VtT = s.VT + k.kth_ddt - k.kappa_ddt * s.V - k.kdt * s.VT + k.xi * uT * Z2
-                      + k.c4T * z2m1;
-        const bool keep = Vt > R(0);
-        s.V = keep ? Vt : R(0);
-        s.Vv = keep ? Vtv : R(0);
-        s.VT = keep ? VtT : R(0);
-    }
-}
-
-__device__ __forceinline__ float norm_cdf(float x) { return normcdff(x); }
-__device__ __forceinline__ double norm_cdf(double x) { return normcdf(x); }
-__device__ __forceinline__ float log_pos(float x) { return lg2_approx(x) * 0.69314718f; }
-__device__ __forceinline__ double log_pos(double x) { return log(x); }
-
-// One QE step (Andersen 2008) with its tangents.  The variance: exact
-// conditional mean m and variance s^2 of the CIR transition, psi = s^2/m^2;
-// psi <= 1.5: V' = a (b + Za)^2, b^2 = 2/psi - 1 + sqrt(2/psi (2/psi - 1)),
-// a = m / (1 + b^2); psi > 1.5: V' = 0 when Phi(-Za) >= 1 - p, else
-// m ln((1 - p)/Phi(-Za)) / (1 - p) with 1 - p = 2 / (psi + 1).  Then
-// ln S' = ln S + r dt + K0 + K1 V + K2 V' + sq ut Zb, ut = sqrt(dt (V + V')/2);
-// Zb does not move the variance, so the Gamma weights are ut Zb and ut^2.
-template <typename R>
-__device__ __forceinline__ void qe_step(PathState<R> &s, R za, R zb, const Coef<R> &k)
-{
-    const R m = k.qmth + s.V * k.qE;
-    const R mv = s.Vv * k.qE;
-    const R mT = k.qmth_T + s.V * k.qE_T + s.VT * k.qE;
-    const R s2 = k.qs0 + s.V * k.qs1;
-    const R s2v = s.Vv * k.qs1;
-    const R s2T = k.qs0_T + s.V * k.qs1_T + s.VT * k.qs1;
-    const R im = R(1) / m;                           // m >= theta (1 - E) > 0
-    const R psi = s2 * im * im;
-    const R psiv = (s2v - R(2) * s2 * mv * im) * im * im;
-    const R psiT = (s2T - R(2) * s2 * mT * im) * im * im;
-    R Vn, Vnv, VnT;
-    if (psi <= R(1.5)) {
-        const R y = R(2) / psi;
-        const R hy2 = R(-0.5) * y * y;               // dy/dpsi
-        const R root = sqrt(y * (y - R(1)));
-        const R b2 = y - R(1) + root;
-        const R db2 = (R(1) + (R(2) * y - R(1)) / (R(2) * root)) * hy2;   // db^2/dpsi
-        const R b = sqrt(b2);
-        const R ia = R(1) / (R(1) + b2);
-        const R a = m * ia;
-        const R b2v = db2 * psiv, b2T = db2 * psiT;
-        const R hb = R(0.5) / b;
-        const R av = (mv - a * b2v) * ia, aT = (mT - a * b2T) * ia;
-        const R bz = b + za;
-        Vn = a * bz * bz;
-        Vnv = bz * (av * bz + R(2) * a * b2v * hb);
-        VnT = bz * (aT * bz + R(2) * a * b2T * hb);
-    } else {
-        const R omp = R(2) / (psi + R(1));           // 1 - p
-        const R q = norm_cdf(-za);                   // 1 - Uv
-        if (q < omp) {
-            const R L = log_pos(omp / q);
-            const R iomp = R(1) / omp;
-            Vn = m * L * iomp;
-            Vnv = mv * L * iomp + R(0.5) * m * psiv * (L - R(1));
-            VnT = mT * L * iomp + R(0.5) * m * psiT * (L - R(1));
-        } else {
-            Vn = R(0); Vnv = R(0); VnT = R(0);
-        }
-    }
-    const R sum = s.V + Vn;
-    const R y = k.qhdt * sum;                        // ut^2
-    const R rs = rsqrt_pos(y);
-    const R ut = y * rs;
-    const R utv = R(0.5) * k.qhdt * (s.Vv + Vnv) * rs;
-    const R utT = R(0.5) * (k.qhddt * sum + k.qhdt * (s.VT + VnT)) * rs;
-    s.GE += ut * zb;
-    s.QE += y;
-    s.X += k.qK0r + k.qK1 * s.V + k.qK2 * Vn + k.sq * ut * zb;
-    s.Xv += k.qK1 * s.Vv + k.qK2 * Vnv + k.sq * utv * zb;
-    s.XT += k.qK0r_T + k.qK12_T * sum + k.qK1 * s.VT + k.qK2 * VnT + k.sq * utT * zb;
-    s.V = Vn; s.Vv = Vnv; s.VT = VnT;
-}
-
-// Scheme of a kernel instantiation: Milstein or Euler with full truncation
-// or the floor, or QE.  Values 0 and 1 are the Milstein truncations.
-enum { STEP_MIL_FULL = 0, STEP_MIL_FLOOR = 1, STEP_EUL_FULL = 2, STEP_EUL_FLOOR = 3, STEP_QE = 4 };
-
-template <typename R, int STEP>
-__device__ __forceinline__ void scheme_step(PathState<R> &s, R za, R zb, const Coef<R> &k)
-{
-    if constexpr (STEP == STEP_QE)
-        qe_step(s, za, zb, k);
-    else if constexpr (sizeof(R) == 4 && (STEP & 1) == HESTON_TRUNC_FULL)
-        milstein_step_f32_full<(STEP >= STEP_EUL_FULL)>(s, za, zb, k);
-    else
-        milstein_step_generic<R, STEP & 1, (STEP >= STEP_EUL_FULL)>(s, za, zb, k);
-}
-
-// Asian monitoring date (first: the first date, which closes the Asian
-// Gamma weight window).
-template <typename R>
-__device__ __forceinline__ void monitor(PathState<R> &s, bool first)
-{
-    const R e = exp_r(s.X);
-    s.sA += e;
-    s.sC += s.sA;
-    s.sAv += e * s.Xv;
-    s.sAT += e * s.XT;
-    if (first) { s.GA = s.GE; s.QA = s.QE; }
-}
-
-// Per-path estimators of contract c: price, delta, gamma, vega, rho, theta.
-// With A the payoff's underlying (S_T or Sbar), phi the payoff and phi' its
-// slope (1{A>K} for calls, -1{A<K} for puts):
-//   price = D phi(A); delta = D phi' A/S0; gamma = D phi' A/S0^2 (lr - 1);
-//   vega = D phi' dA/dv0; rho = -T price + D phi' dA/dr; theta = r price - D phi' dA/dT.
-// For the European call rho reduces to D K T 1{S_T > K} (Eq. euro_pw).
-template <typename R>
-__device__ __forceinline__ void estimators(const PathState<R> &s, const ContractSet<R> &cs, int c,
-                                           R eT, R est[6])
-{
-    const R K = cs.K[c], D = cs.D, T = cs.T;
-    const bool euro = cs.payoff[c] == HESTON_EUROPEAN;
-    R A, dAv, dAT, dAr, lr;
-    if (euro) {
-        A = cs.S0 * eT;
-        dAv = A * s.Xv;
-        dAT = A * s.XT;
-        dAr = T * A;
-        lr = s.GE * cs.inv_sq / s.QE;
-    } else {
-        A = cs.S0_over_M * s.sA;
-        dAv = cs.S0_over_M * s.sAv;
-        dAT = cs.S0_over_M * s.sAT;
-        dAr = cs.dAr_scale * (cs.Mp1 * s.sA - s.sC);
-        lr = s.GA * cs.inv_sq / s.QA;
-    }
-    R pay, slope;
-    if (!cs.is_put[c]) {
-        slope = A > K ? R(1) : R(0);
-        pay = A > K ? A - K : R(0);
-    } else {
-        slope = A < K ? R(-1) : R(0);
-        pay = A < K ? K - A : R(0);
-    }
-    const R Dslope = D * slope;
-    est[0] = D * pay;
-    est[1] = Dslope * A * cs.inv_S0;
-    est[2] = Dslope * A * cs.inv_S0sq * (lr - R(1));
-    est[3] = Dslope * dAv;
-    est[4] = euro ? Dslope * K * T : Dslope * dAr - T * est[0];
-    est[5] = cs.r * est[0] - Dslope * dAT;
-}
-
-template <typename R>
-__device__ __forceinline__ R warp_sum(R v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// Asian monitoring layout: none, a date after every step, or every `stride` steps.
-enum { MON_NONE = 0, MON_EVERY = 1, MON_STRIDE = 2 };
-
-// Run NP paths (one lane) through all N steps.  Step k uses Philox counter
-// (k/2, path_lo, path_hi, 0): words (x, y) for even k, (z, w) for odd k.
-template <typename R, int STEP, int MON, int NP>
-__device__ __forceinline__ void simulate(PathState<R> (&s)[NP], const uint32_t (&plo)[NP],
-                                         const uint32_t (&phi)[NP], const Coef<R> &k,
-                                         const ContractSet<R> &cs, PhiloxKey key, uint32_t N)
-{
-#pragma unroll
-    for (int q = 0; q < NP; ++q) init_state(s[q], k.v0);
-    const uint32_t stride = cs.stride;
-    uint32_t next_mon = stride;
-    const uint32_t n_pairs = N >> 1;
-    for (uint32_t j = 0; j < n_pairs; ++j) {
-        uint4 w[NP];
-#pragma unroll
-        for (int q = 0; q < NP; ++q) w[q] = philox4x32_10(make_uint4(j, plo[q], phi[q], 0u), key);
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-#pragma unroll
-            for (int q = 0; q < NP; ++q) {
-                R za, zb;
-                if (h == 0) box_muller(w[q].x, w[q].y, za, zb);
-                else        box_muller(w[q].z, w[q].w, za, zb);
-                scheme_step<R, STEP>(s[q], za, zb, k);
-            }
-            const uint32_t kp1 = 2u * j + 1u + (uint32_t)h;
-            if (MON == MON_EVERY) {
-                const bool first = (h == 0) && (j == 0);
-#pragma unroll
-                for (int q = 0; q < NP; ++q) monitor(s[q], first);
-            } else if (MON == MON_STRIDE) {
-                if (kp1 == next_mon) {
-#pragma unroll
-                    for (int q = 0; q < NP; ++q) monitor(s[q], kp1 == stride);
-                    next_mon += stride;
-                }
-            }
-        }
-    }
-    if (N & 1u) {
-#pragma unroll
-        for (int q = 0; q < NP; ++q) {
-            const uint4 w = philox4x32_10(make_uint4(n_pairs, plo[q], phi[q], 0u), key);
-            R za, zb;
-            box_muller(w.x, w.y, za, zb);
-            scheme_step<R, STEP>(s[q], za, zb, k);
-        }
-        if (MON == MON_EVERY || (MON == MON_STRIDE && N == next_mon)) {
-#pragma unroll
-            for (int q = 0; q < NP; ++q) monitor(s[q], N == stride);
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// K1: path kernel.  Warp w handles tiles w, w + n_warps, ...; lane l carries
-// paths tile*64 + l and tile*64 + l + 32.  Per tile and estimator it writes
-// sum_x and sum_x^2 (the lane's two paths added first, then a fixed xor
-// butterfly), so tile rows do not depend on the launch shape.
-// ---------------------------------------------------------------------------
-template <typename R, int STEP, int MON>
-__global__ void __launch_bounds__(kPathBlock) heston_paths_kernel(Coef<R> k, ContractSet<R> cs, Launch a)
-{
-    const int lane = threadIdx.x & 31;
-    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    const int nc = cs.n;
-    const int width = 12 * nc;
-
-    for (uint64_t tile = warp; tile < a.n_tiles; tile += n_warps) {
-        PathState<R> s[2];
-        uint32_t plo[2], phi[2];
-        bool keep[2];
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const uint64_t local = tile * kTile + (uint64_t)lane + 32u * (uint64_t)q;
-            keep[q] = local < a.n_paths;                      // ragged last tile
-            const uint64_t g = a.path_begin + local;
-            plo[q] = (uint32_t)g;
-            phi[q] = (uint32_t)(g >> 32);
-        }
-        simulate<R, STEP, MON, 2>(s, plo, phi, k, cs, a.key, a.N);
-
-        R eT[2];
-#pragma unroll
-        for (int q = 0; q < 2; ++q) eT[q] = exp_r(s[q].X);
-        double *row = a.tile_sums + tile * (uint64_t)width;
-#pragma unroll
-        for (int c = 0; c < kMaxC; ++c) {
-            if (c >= nc) break;
-            R e0[6], e1[6];
-            estimators(s[0], cs, c, eT[0], e0);
-            estimators(s[1], cs, c, eT[1], e1);
-#pragma unroll
-            for (int j = 0; j < 6; ++j) {
-                const R x0 = keep[0] ? e0[j] : R(0), x1 = keep[1] ? e1[j] : R(0);
-                const R sx = warp_sum(x0 + x1);
-                const R sxx = warp_sum(x0 * x0 + x1 * x1);
-                if (lane == j) row[c * 6 + j] = (double)sx;
-                if (lane == 6 + j) row[6 * nc + c * 6 + j] = (double)sxx;
-            }
-        }
-    }
-}
-
-// Per-path record (see heston_mc_debug_paths) and estimators of one path.
-template <typename R>
-__device__ void write_debug_record(const PathState<R> &s, const ContractSet<R> &cs, double *o,
-                                   double *est)
-{
-    const R eT = exp_r(s.X);
-    const double S0 = (double)cs.S0, M = (double)cs.M;
-    o[0] = (double)s.X;   o[1] = (double)s.V;
-    o[2] = (double)s.Xv;  o[3] = (double)s.Vv;
-    o[4] = (double)s.XT;  o[5] = (double)s.VT;
-    o[6] = S0 * (double)s.sA;
-    o[7] = S0 * ((double)cs.T / M) * ((M + 1.0) * (double)s.sA - (double)s.sC);
-    o[8] = S0 * (double)s.sAv;
-    o[9] = S0 * (double)s.sAT;
-    o[10] = (double)s.GE; o[11] = (double)s.QE;
-    o[12] = (double)s.GA; o[13] = (double)s.QA;
-    o[14] = 0.0;
-    for (int c = 0; c < cs.n; ++c) {
-        R e[6];
-        estimators(s, cs, c, eT, e);
-        for (int j = 0; j < 6; ++j) est[c * 6 + j] = (double)e[j];
-    }
-}
-
-// Test kernel: one thread per requested path, the same step code, writes the
-// per-path record and estimators.
-template <typename R, int STEP, int MON>
-__global__ void heston_debug_kernel(Coef<R> k, ContractSet<R> cs, PhiloxKey key, uint32_t N,
-                                    const uint64_t *paths, uint32_t count, double *rec, double *est)
-{
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= count) return;
-    const uint64_t g = paths[i];
-    PathState<R> s[1];
-    const uint32_t plo[1] = {(uint32_t)g}, phi[1] = {(uint32_t)(g >> 32)};
-    simulate<R, STEP, MON, 1>(s, plo, phi, k, cs, key, N);
-    write_debug_record(s[0], cs, rec + (uint64_t)i * kRecordDoubles, est + (uint64_t)i * cs.n * 6);
-}
-
-template <typename R>
-__global__ void rng_debug_kernel(PhiloxKey key, const uint64_t *paths, const uint32_t *steps,
-                                 uint32_t count, uint32_t *words, double *normals)
-{
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= count) return;
-    const uint64_t g = paths[i];
-    const uint32_t st = steps[i];
-    const uint4 w = philox4x32_10(make_uint4(st >> 1, (uint32_t)g, (uint32_t)(g >> 32), 0u), key);
-    words[4 * i + 0] = w.x; words[4 * i + 1] = w.y;
-    words[4 * i + 2] = w.z; words[4 * i + 3] = w.w;
-    R za, zb;
-    if (st & 1u) box_muller(w.z, w.w, za, zb);
-    else         box_muller(w.x, w.y, za, zb);
-    normals[2 * i] = (double)za;
-    normals[2 * i + 1] = (double)zb;
-}
-
-
-// ---------------------------------------------------------------------------
-// Randomised quasi-Monte Carlo normals (Sec. 2.7): a Sobol sequence with
-// digital shifts, fed through a Brownian bridge so that the first dimensions
-// carry the coarse shape of both Brownian motions.  Definitions (the test
-// oracle implements the same ones separately):
-//   * dimension 0: v_k = 2^(32-k); dimension j >= 1: the j-th primitive
-//     polynomial over GF(2) ordered by (degree, coefficient bits), initial
-//     m_1..m_s from Philox (key 0x50B01, counter ((k-1)/4, j, c, 3), word
-//     (k-1)%4, m_k = 2 (w mod 2^(k-1)) + 1); for j < 32 the first candidate c
-//     that keeps the leading (j+1)x(j+1) first-digit matrix non-singular
-//     over GF(2) (Property A), else c = 0; Bratley-Fox recurrence.
-//   * replicate r's shift of dimension d: Philox (seed key) counter
-//     (d/4, r, 0, 2), word d%4; y = x_d(point) XOR shift.
-//   * u = ((y >> 8) + 1/2) 2^-24, z = Phi^-1(u).
-//   * Brownian bridge on the step grid 0..N: node 0 = time N; then
-//     breadth-first bisection m = l + (r-l)/2 of intervals with r - l >= 2.
-//     Node j drives motion a with dimension 2j and motion b with 2j+1.
-// In the kernel the bridge runs in time order: a per-thread stack holds W at
-// the right ends of the open intervals.  Entering step k (W_k known), the
-// plan pushes W_m = W_k + (m-k)/(r-k) (W_r - W_k) + sqrt((m-k)(r-m)/(r-k)) z
-// for the nodes m of [k, r] down to [k, k+1] (r: the stack top), then pops
-// W_{k+1}; the step normal is W_{k+1} - W_k.  Every W is interpolated from
-// two stored values, so FP32 rounding does not accumulate along the path.
-// ---------------------------------------------------------------------------
-constexpr int kQmcMaxLevels = 14;           // stack slots (slot 0 = 0); n_steps <= 2048
-constexpr uint32_t kQmcMaxSteps = 2048;
-constexpr uint32_t kSobolKey0 = 0x50B01u, kSobolKey1 = 0u;
-constexpr uint32_t kSobolInitTag = 3u, kSobolShiftTag = 2u;
-
-struct BridgeOp {
-    int32_t node;       // node j: normals from dimensions 2j and 2j+1
-    float a;            // (m - k) / (r - k)
-    float s;            // sqrt((m - k)(r - m) / (r - k)); node 0: a = 0, s = sqrt(N)
-    int32_t pad;
-};
-
-struct QmcTables {
-    const uint32_t *V;        // [D][32] direction integers
-    const uint32_t *T;        // [D][64] x_d(p) for the 64 points p of a tile
-    const BridgeOp *ev;       // stack pushes, step-major
-    const int32_t *ev_off;    // [N + 1] first push of each step
-};
-
-struct QmcLaunch {
-    QmcTables tb;
-    const uint32_t *U;        // [tiles per replicate][D]: x_d(64 t), high bits of the point
-    const uint32_t *shift;    // [replicates][D]
-    uint32_t D, N, tpr;       // Sobol dims (2N), steps, tiles per replicate
-    uint64_t n_tiles;
-    double *tile_sums;
-};
-
-// Phi^-1 of the 24-bit uniform of y, taking the lower half by symmetry so that
-// the FP32 uniform (2k + 1) 2^-25 is exact and never 1.
-__device__ __forceinline__ float qmc_normal(uint32_t y)
-{
-    const uint32_t k = y >> 8;
-    const bool upper = k >= 0x800000u;
-    const uint32_t kk = upper ? 0xFFFFFFu - k : k;
-    const float u = (float)(2u * kk + 1u) * 2.98023223876953125e-8f;
-    const float z = normcdfinvf(u);
-    return upper ? -z : z;
-}
-
-// NP paths of one lane through all N steps with bridge normals.  pos[q]: the
-// path's position in its 64-point tile; U / Sh: the tile's high-bit Sobol
-// integers and the replicate's shifts.
-template <int TRUNC, int MON, int NP>
-__device__ __forceinline__ void simulate_qmc(PathState<float> (&s)[NP], const uint32_t (&pos)[NP],
-                                             const Coef<float> &k, const ContractSet<float> &cs,
-                                             const QmcTables &tb, const uint32_t *U,
-                                             const uint32_t *Sh, uint32_t N)
-{
-    float st[NP][2][kQmcMaxLevels];             // W at pending right ends; slot 0 = 0
-    float Wk[NP][2];                            // W at the current time
-#pragma unroll
-    for (int q = 0; q < NP; ++q) {
-        init_state(s[q], k.v0);
-        Wk[q][0] = 0.0f;
-        Wk[q][1] = 0.0f;
-        st[q][0][0] = 0.0f;
-        st[q][1][0] = 0.0f;
-    }
-    int top = 0;
-    const uint32_t stride = cs.stride;
-    uint32_t next_mon = stride;
-    for (uint32_t kk = 0; kk < N; ++kk) {
-        const int e1 = tb.ev_off[kk + 1];
-        for (int e = tb.ev_off[kk]; e < e1; ++e) {
-            const BridgeOp op = tb.ev[e];
-#pragma unroll
-            for (int mu = 0; mu < 2; ++mu) {
-                const uint32_t dim = 2u * (uint32_t)op.node + (uint32_t)mu;
-                const uint32_t hi = U[dim] ^ Sh[dim];
-#pragma unroll
-                for (int q = 0; q < NP; ++q) {
-                    const float z = qmc_normal(tb.T[dim * 64u + pos[q]] ^ hi);
-                    const float Wr = st[q][mu][top];
-                    st[q][mu][top + 1] = fmaf(op.s, z, fmaf(op.a, Wr - Wk[q][mu], Wk[q][mu]));
-                }
-            }
-            ++top;
-        }
-        float za[NP], zb[NP];
-#pragma unroll
-        for (int q = 0; q < NP; ++q) {
-            const float wa = st[q][0][top], wb = st[q][1][top];
-            za[q] = wa - Wk[q][0];
-            zb[q] = wb - Wk[q][1];
-            Wk[q][0] = wa;
-            Wk[q][1] = wb;
-        }
-        --top;
-#pragma unroll
-        for (int q = 0; q < NP; ++q) scheme_step<float, TRUNC>(s[q], za[q], zb[q], k);
-        const uint32_t kp1 = kk + 1u;
-        if (MON == MON_EVERY) {
-#pragma unroll
-            for (int q = 0; q < NP; ++q) monitor(s[q], kk == 0);
-        } else if (MON == MON_STRIDE) {
-            if (kp1 == next_mon) {
-#pragma unroll
-                for (int q = 0; q < NP; ++q) monitor(s[q], kp1 == stride);
-                next_mon += stride;
-            }
-        }
-    }
-}
-
-// QMC path kernel: same tile layout and epilogue as heston_paths_kernel.
-// Tile t belongs to replicate t / tpr; every tile is full (points per
-// replicate are a multiple of 64).
-template <int TRUNC, int MON>
-__global__ void __launch_bounds__(kPathBlock) heston_qmc_kernel(Coef<float> k, ContractSet<float> cs,
-                                                                QmcLaunch a)
-{
-    const int lane = threadIdx.x & 31;
-    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    const int nc = cs.n;
-    const int width = 12 * nc;
-    for (uint64_t tile = warp; tile < a.n_tiles; tile += n_warps) {
-        const uint32_t rep = (uint32_t)(tile / a.tpr), tin = (uint32_t)(tile % a.tpr);
-        PathState<float> s[2];
-        const uint32_t pos[2] = {(uint32_t)lane, (uint32_t)lane + 32u};
-        simulate_qmc<TRUNC, MON, 2>(s, pos, k, cs, a.tb, a.U + (uint64_t)tin * a.D,
-                                    a.shift + (uint64_t)rep * a.D, a.N);
-        float eT[2];
-#pragma unroll
-        for (int q = 0; q < 2; ++q) eT[q] = exp_r(s[q].X);
-        double *row = a.tile_sums + tile * (uint64_t)width;
-#pragma unroll
-        for (int c = 0; c < kMaxC; ++c) {
-            if (c >= nc) break;
-            float e0[6], e1[6];
-            estimators(s[0], cs, c, eT[0], e0);
-            estimators(s[1], cs, c, eT[1], e1);
-#pragma unroll
-            for (int j = 0; j < 6; ++j) {
-                const float sx = warp_sum(e0[j] + e1[j]);
-                const float sxx = warp_sum(e0[j] * e0[j] + e1[j] * e1[j]);
-                if (lane == j) row[c * 6 + j] = (double)sx;
-                if (lane == 6 + j) row[6 * nc + c * 6 + j] = (double)sxx;
-            }
-        }
-    }
-}
-
-// Per-launch tables: U[t][d] = x_d(64 t) and the replicates' digital shifts.
-__global__ void qmc_setup_kernel(const uint32_t *V, uint32_t D, uint32_t tpr, uint32_t R,
-                                 PhiloxKey key, uint32_t *U, uint32_t *shift)
-{
-    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const uint64_t nU = (uint64_t)tpr * D;
-    if (i < nU) {
-        const uint32_t t = (uint32_t)(i / D), d = (uint32_t)(i % D);
-        const uint64_t n = (uint64_t)t * 64u;
-        uint32_t x = 0;
-        for (int b = 6; b < 32; ++b)
-            if ((n >> b) & 1u) x ^= V[d * 32u + b];
-        U[i] = x;
-    } else if (i < nU + (uint64_t)R * D) {
-        const uint64_t j = i - nU;
-        const uint32_t r = (uint32_t)(j / D), d = (uint32_t)(j % D);
-        const uint4 w = philox4x32_10(make_uint4(d >> 2, r, 0u, kSobolShiftTag), key);
-        const uint32_t sel = d & 3u;
-        shift[j] = sel == 0 ? w.x : sel == 1 ? w.y : sel == 2 ? w.z : w.w;
-    }
-}
-
-// Test support: Udbg[i][d] = x_d(points[i] with its low 6 bits cleared).
-__global__ void qmc_debug_high_bits_kernel(const uint32_t *V, uint32_t D, const uint32_t *points,
-                                           uint32_t count, uint32_t *Udbg)
-{
-    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (uint64_t)count * D) return;
-    const uint32_t p = (uint32_t)(i / D), d = (uint32_t)(i % D);
-    const uint32_t n = points[p];
-    uint32_t x = 0;
-    for (int b = 6; b < 32; ++b)
-        if ((n >> b) & 1u) x ^= V[d * 32u + b];
-    Udbg[i] = x;
-}
-
-// Test kernel: one thread per requested point of one replicate, through the
-// same simulate_qmc as the path kernel.
-template <int TRUNC, int MON>
-__global__ void heston_qmc_debug_kernel(Coef<float> k, ContractSet<float> cs, QmcTables tb,
-                                        uint32_t N, const uint32_t *points, const uint32_t *Udbg,
-                                        const uint32_t *shift_row, uint32_t count, double *rec,
-                                        double *est)
-{
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= count) return;
-    PathState<float> s[1];
-    const uint32_t pos[1] = {points[i] & 63u};
-    simulate_qmc<TRUNC, MON, 1>(s, pos, k, cs, tb, Udbg + (uint64_t)i * 2u * N, shift_row, N);
-    write_debug_record(s[0], cs, rec + (uint64_t)i * kRecordDoubles, est + (uint64_t)i * cs.n * 6);
-}
-
-__global__ void reduce_replicates_kernel(const double *tile_sums, uint32_t tpr, int width,
-                                         double *rep_sums)
-{
-    const uint64_t r = blockIdx.x;
-    for (int col = threadIdx.x; col < width; col += blockDim.x) {
-        double acc = 0.0;
-        for (uint32_t t = 0; t < tpr; ++t) acc += tile_sums[(r * tpr + t) * (uint64_t)width + col];
-        rep_sums[r * width + col] = acc;
-    }
-}
-
-// Randomised-QMC estimate: mean over replicates of the replicate averages;
-// SE = their sample stdev / sqrt(R).
-__global__ void reduce_final_qmc_kernel(const double *rep_sums, uint32_t R, int n_contracts,
-                                        double ppr, int gamma_nan, double *out)
-{
-    const int width = 12 * n_contracts;
-    const int E = 6 * n_contracts;
-    for (int e = threadIdx.x; e < E; e += blockDim.x) {
-        double mean = 0.0;
-        for (uint32_t r = 0; r < R; ++r) mean += rep_sums[(uint64_t)r * width + e] / ppr;
-        mean /= (double)R;
-        double var = 0.0;
-        for (uint32_t r = 0; r < R; ++r) {
-            const double d = rep_sums[(uint64_t)r * width + e] / ppr - mean;
-            var += d * d;
-        }
-        var /= (double)(R - 1);
-        double se = sqrt(var / (double)R);
-        const int c = e / 6, j = e % 6;
-        if (gamma_nan && j == 2) { mean = nan(""); se = nan(""); }
-        out[c * 12 + j] = mean;
-        out[c * 12 + 6 + j] = se;
-    }
-}
-
-// ---------------------------------------------------------------------------
-// K2: fixed-order FP64 reduction.  Level 1: group g sums tiles
-// [g*256, (g+1)*256) column by column in tile order.  Level 2: one CTA sums
-// the groups in order and forms mean and standard error per estimator.
-// ---------------------------------------------------------------------------
-// Column sums of tile rows [lo, hi) in row order (one group of <= 256 tiles).
-__device__ __forceinline__ void sum_rows(const double *rows, uint64_t lo, uint64_t hi, int width,
-                                         double *out_row)
-{
-    for (int col = threadIdx.x; col < width; col += blockDim.x) {
-        double acc = 0.0;
-        for (uint64_t t = lo; t < hi; ++t) acc += rows[t * width + col];
-        out_row[col] = acc;
-    }
-}
-
-// Sum n_groups group rows in order and write mean / SE per estimator.
-__device__ __forceinline__ void finish_groups(const double *group_sums, uint64_t n_groups,
-                                              int n_contracts, double n_paths, int gamma_nan,
-                                              double *out)
-{
-    __shared__ double tot[12 * kMaxC];
-    const int width = 12 * n_contracts;
-    const int E = 6 * n_contracts;
-    for (int col = threadIdx.x; col < width; col += blockDim.x) {
-        double acc = 0.0;
-        for (uint64_t g = 0; g < n_groups; ++g) acc += group_sums[g * width + col];
-        tot[col] = acc;
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < E; e += blockDim.x) {
-        const int c = e / 6, j = e % 6;
-        const double mean = tot[e] / n_paths;
-        const double var = (tot[E + e] - n_paths * mean * mean) / (n_paths - 1.0);
-        double se = sqrt(var > 0.0 ? var / n_paths : 0.0);
-        double m = mean;
-        if (gamma_nan && j == 2) { m = nan(""); se = nan(""); }
-        out[c * 12 + j] = m;
-        out[c * 12 + 6 + j] = se;
-    }
-}
-
-__global__ void reduce_groups_kernel(const double *tile_sums, uint64_t n_tiles, int width,
-                                     double *group_sums)
-{
-    const uint64_t g = blockIdx.x;
-    const uint64_t lo = g * kGroupTiles;
-    const uint64_t hi = lo + kGroupTiles < n_tiles ? lo + kGroupTiles : n_tiles;
-    sum_rows(tile_sums, lo, hi, width, group_sums + g * width);
-}
-
-__global__ void reduce_final_kernel(const double *group_sums, uint64_t n_groups, int n_contracts,
-                                    double n_paths, int gamma_nan, double *out)
-{
-    finish_groups(group_sums, n_groups, n_contracts, n_paths, gamma_nan, out);
-}
-
-// ---------------------------------------------------------------------------
-// Batched persistent launch: many contracts, each with its own parameters,
-// path count, step count and seed, in one launch.  Work items are
-// (contract, 64-path tile) pairs handed out through an atomic counter,
-// contracts with the most steps first; each contract's tile rows and their
-// reduction (sum_rows / finish_groups) are those of its own launch, so every
-// result equals the contract's own launch bit for bit.  A device status word
-// lets a caller stop the launch between work items: 0 = run, 1 = cancel
-// requested, 2 = the kernel saw the request and took no further work.
-// ---------------------------------------------------------------------------
-struct BatchItemDev {
-    Coef<float> k;
-    ContractSet<float> cs;        // one contract
-    PhiloxKey key;
-    uint64_t n_paths;
-    uint64_t n_tiles;
-    uint64_t row_begin;           // first tile row of this contract
-    uint64_t group_begin;         // first group row of this contract
-    uint32_t N;
-    int32_t mon;
-    int32_t gamma_nan;
-    int32_t pad;
-};
-
-struct BatchLaunch {
-    const BatchItemDev *items;    // caller order
-    const uint64_t *work_begin;   // [n_items] first work index of the p-th contract in work order
-    const uint32_t *work_item;    // [n_items] contract of the p-th position in work order
-    const uint64_t *work_tile0;   // [n_items] first tile of the p-th position (NULL = 0)
-    const uint64_t *group_begin;  // [n_items] (caller order) first group row, for the reductions
-    uint32_t n_items;
-    uint64_t total_work;
-    unsigned long long *counter;
-    int32_t *status;
-    double *rows;
-};
-
-template <int TRUNC>
-__global__ void __launch_bounds__(kPathBlock) heston_batch_kernel(BatchLaunch a)
-{
-    const int lane = threadIdx.x & 31;
-    bool saw_cancel = false;
-    while (true) {
-        unsigned long long g = ~0ull;
-        if (lane == 0) {
-            const int32_t st = a.status ? *(volatile int32_t *)a.status : 0;
-            if (st != 0) saw_cancel = true;
-            else g = atomicAdd(a.counter, 1ull);
-        }
-        g = __shfl_sync(0xffffffffu, g, 0);
-        if (g >= a.total_work) break;
-        uint32_t lo = 0, hi = a.n_items;
-        while (hi - lo > 1) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if (a.work_begin[mid] <= g) lo = mid; else hi = mid;
-        }
-        const BatchItemDev &it = a.items[a.work_item[lo]];
-        const uint64_t t = g - a.work_begin[lo] + (a.work_tile0 ? a.work_tile0[lo] : 0ull);
-        const Coef<float> k = it.k;
-        const PhiloxKey key = it.key;
-        PathState<float> s[2];
-        uint32_t plo[2], phi[2];
-        bool keep[2];
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const uint64_t local = t * kTile + (uint64_t)lane + 32u * (uint64_t)q;
-            keep[q] = local < it.n_paths;
-            plo[q] = (uint32_t)local;
-            phi[q] = (uint32_t)(local >> 32);
-        }
-        if (it.mon == MON_NONE)       simulate<float, TRUNC, MON_NONE, 2>(s, plo, phi, k, it.cs, key, it.N);
-        else if (it.mon == MON_EVERY) simulate<float, TRUNC, MON_EVERY, 2>(s, plo, phi, k, it.cs, key, it.N);
-        else                          simulate<float, TRUNC, MON_STRIDE, 2>(s, plo, phi, k, it.cs, key, it.N);
-        float e0[6], e1[6];
-        estimators(s[0], it.cs, 0, exp_r(s[0].X), e0);
-        estimators(s[1], it.cs, 0, exp_r(s[1].X), e1);
-        double *row = a.rows + (it.row_begin + t) * 12u;
-#pragma unroll
-        for (int j = 0; j < 6; ++j) {
-            const float x0 = keep[0] ? e0[j] : 0.0f, x1 = keep[1] ? e1[j] : 0.0f;
-            const float sx = warp_sum(x0 + x1);
-            const float sxx = warp_sum(x0 * x0 + x1 * x1);
-            if (lane == j) row[j] = (double)sx;
-            if (lane == 6 + j) row[6 + j] = (double)sxx;
-        }
-    }
-    if (saw_cancel) atomicCAS(a.status, 1, 2);
-}
-
-// One block per group row of the whole batch: the contract is found from
-// the flat group index.
-__global__ void batch_reduce_groups_kernel(const BatchItemDev *items, const uint64_t *group_begin,
-                                           uint32_t n_items, const double *rows, double *groups)
-{
-    const uint64_t g = blockIdx.x;
-    uint32_t lo = 0, hi = n_items;
-    while (hi - lo > 1) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (group_begin[mid] <= g) lo = mid; else hi = mid;
-    }
-    const BatchItemDev &it = items[lo];
-    const uint64_t j = g - it.group_begin;
-    const uint64_t t0 = j * kGroupTiles;
-    const uint64_t t1 = t0 + kGroupTiles < it.n_tiles ? t0 + kGroupTiles : it.n_tiles;
-    sum_rows(rows + it.row_begin * 12u, t0, t1, 12, groups + g * 12u);
-}
-
-__global__ void batch_reduce_final_kernel(const BatchItemDev *items, const double *groups, double *out)
-{
-    const BatchItemDev &it = items[blockIdx.x];
-    const uint64_t ng = (it.n_tiles + kGroupTiles - 1) / kGroupTiles;
-    finish_groups(groups + it.group_begin * 12u, ng, 1, (double)it.n_paths, it.gamma_nan,
-                  out + (uint64_t)blockIdx.x * 12u);
-}
-
-
-// ---------------------------------------------------------------------------
-// Adjoint (reverse-mode pathwise) gradient of the price with respect to
-// (S0, v0, kappa, theta, xi, rho, r), full truncation, FP32 paths, FP64 sums.
-// The forward kernel prices and stores, per path, (X, V) every C = ceil(sqrt N)
-// steps plus the payoff seed; the backward kernel rebuilds each C-step segment
-// from its checkpoint (normals recomputed from the Philox counters) and sweeps
-// the adjoints of the Milstein step (Sec. 2.4.2) in reverse:
-//   X' = X + (r - V+/2) dt + u Za,   u = sqrt(V+ dt),   Z2 = rho Za + s Zb,
-//   V' = V + kappa (theta - V+) dt + xi u Z2 + xi^2 dt (Z2^2 - 1) 1{V>0} / 4,
-// with P = e^{-rT} phi(A), A = S0 e^{X_N} or (S0/M) sum_i e^{X(t_i)}.
-// ---------------------------------------------------------------------------
-constexpr int kAdjMaxSeg = 32;             // segment length C <= 32: n_steps <= 1024
-
-struct AdjLaunch {
-    PhiloxKey key;
-    uint64_t n_paths, n_tiles;
-    uint32_t N, C, n_seg;                   // steps, segment length, segments
-    float2 *ckpt;                           // [n_seg][n_paths] (X, V) at each segment start
-    float2 *seed;                           // [n_paths] (payoff, D phi'(A) / M or D phi'(S_T))
-    double *rows;                           // tile rows
-};
-
-// Normals of step k of a path (words by parity, as in simulate()).
-__device__ __forceinline__ void step_normals(PhiloxKey key, uint32_t plo, uint32_t phi, uint32_t k,
-                                             float &za, float &zb)
-{
-    const uint4 w = philox4x32_10(make_uint4(k >> 1, plo, phi, 0u), key);
-    if (k & 1u) box_muller(w.z, w.w, za, zb);
-    else        box_muller(w.x, w.y, za, zb);
-}
-
-// One plain Milstein step (no tangents), full truncation: the forward of the adjoint.
-__device__ __forceinline__ void plain_step(float &X, float &V, float za, float zb, const Coef<float> &k)
-{
-    const float Z2 = fmaf(k.rho, za, k.sq * zb);
-    const bool pos = V > 0.0f;
-    const float Vp = fmaxf(V, 0.0f);
-    const float u = sqrt_approx(Vp * k.dt);
-    X = fmaf(u, za, fmaf(fmaf(-0.5f, Vp, k.r), k.dt, X));
-    const float z2m1 = fmaf(Z2, Z2, -1.0f);
-    V = fmaf(pos ? k.c4 : 0.0f, z2m1, fmaf(k.xi * Z2, u, fmaf(-k.kdt, Vp, V + k.kth_dt)));
-}
-
-template <int MON>
-__global__ void __launch_bounds__(kPathBlock) heston_adj_fwd_kernel(Coef<float> k, ContractSet<float> cs,
-                                                                    AdjLaunch a)
-{
-    const int lane = threadIdx.x & 31;
-    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    for (uint64_t tile = warp; tile < a.n_tiles; tile += n_warps) {
-        float x[2];
-#pragma unroll 1
-        for (int q = 0; q < 2; ++q) {
-            const uint64_t path = tile * kTile + (uint64_t)lane + 32u * (uint64_t)q;
-            const bool keep = path < a.n_paths;
-            const uint32_t plo = (uint32_t)path, phi = (uint32_t)(path >> 32);
-            float X = 0.0f, V = k.v0, sA = 0.0f;
-            for (uint32_t kk = 0; kk < a.N; ++kk) {
-                if (keep && kk % a.C == 0) a.ckpt[(uint64_t)(kk / a.C) * a.n_paths + path] = make_float2(X, V);
-                float za, zb;
-                step_normals(a.key, plo, phi, kk, za, zb);
-                plain_step(X, V, za, zb, k);
-                if (MON != MON_NONE && (kk + 1) % cs.stride == 0) sA += exp_r(X);
-            }
-            const float A = MON == MON_NONE ? cs.S0 * exp_r(X) : cs.S0_over_M * sA;
-            const float K = cs.K[0];
-            float pay, slope;
-            if (!cs.is_put[0]) { slope = A > K ? 1.0f : 0.0f; pay = A > K ? A - K : 0.0f; }
-            else               { slope = A < K ? -1.0f : 0.0f; pay = A < K ? K - A : 0.0f; }
-            const float scale = MON == MON_NONE ? 1.0f : 1.0f / (float)cs.M;
-            if (keep) a.seed[path] = make_float2(cs.D * pay, cs.D * slope * scale);
-            x[q] = keep ? cs.D * pay : 0.0f;
-        }
-        const float sx = warp_sum(x[0] + x[1]);
-        const float sxx = warp_sum(x[0] * x[0] + x[1] * x[1]);
-        if (lane == 0) { a.rows[tile * 2] = (double)sx; a.rows[tile * 2 + 1] = (double)sxx; }
-    }
-}
-
-template <int MON>
-__global__ void __launch_bounds__(kPathBlock) heston_adj_bwd_kernel(Coef<float> k, ContractSet<float> cs,
-                                                                    AdjLaunch a, float T)
-{
-    const int lane = threadIdx.x & 31;
-    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    const float inv_sq = 1.0f / k.sq;
-    for (uint64_t tile = warp; tile < a.n_tiles; tile += n_warps) {
-        float g[2][7];
-#pragma unroll 1
-        for (int q = 0; q < 2; ++q) {
-            const uint64_t path = tile * kTile + (uint64_t)lane + 32u * (uint64_t)q;
-            const bool keep = path < a.n_paths;
-            const uint64_t pidx = keep ? path : 0;          // a valid index for the loads
-            const uint32_t plo = (uint32_t)path, phi = (uint32_t)(path >> 32);
-            const float2 sd = a.seed[pidx];
-            const float aseed = sd.y;                       // dP/dS_i (Asian) or dP/dS_T
-            float gS0 = 0.0f, gk = 0.0f, gth = 0.0f, gxi = 0.0f, grho = 0.0f, gr = 0.0f;
-            float Xb = 0.0f, Vb = 0.0f;                     // adjoints of the state after the step
-            float Xs[kAdjMaxSeg + 1], Vs[kAdjMaxSeg], Zas[kAdjMaxSeg], Zbs[kAdjMaxSeg];
-            for (int seg = (int)a.n_seg - 1; seg >= 0; --seg) {
-                const uint32_t k0 = (uint32_t)seg * a.C;
-                const uint32_t k1 = min(a.N, k0 + a.C);
-                const float2 c0 = a.ckpt[(uint64_t)seg * a.n_paths + pidx];
-                float X = c0.x, V = c0.y;
-                Xs[0] = X;
-                for (uint32_t kk = k0; kk < k1; ++kk) {
-                    float za, zb;
-                    step_normals(a.key, plo, phi, kk, za, zb);
-                    const uint32_t i = kk - k0;
-                    Vs[i] = V; Zas[i] = za; Zbs[i] = zb;
-                    plain_step(X, V, za, zb, k);
-                    Xs[i + 1] = X;
-                }
-                for (int i = (int)(k1 - k0) - 1; i >= 0; --i) {
-                    const uint32_t kp1 = k0 + (uint32_t)i + 1u;
-                    // the payoff's dependence on X_{k+1}
-                    const bool date = MON == MON_NONE ? kp1 == a.N : (kp1 % cs.stride == 0);
-                    if (date) {
-                        const float e = exp_r(Xs[i + 1]);
-                        Xb = fmaf(aseed * cs.S0, e, Xb);
-                        gS0 = fmaf(aseed, e, gS0);
-                    }
-                    const float za = Zas[i], zb = Zbs[i], Vk = Vs[i];
-                    const float Z2 = fmaf(k.rho, za, k.sq * zb);
-                    const bool pos = Vk > 0.0f;
-                    const float Vp = fmaxf(Vk, 0.0f);
-                    const float y = Vp * k.dt;
-                    const float rs = rsqrt_approx(fmaxf(y, 1e-30f));
-                    const float u = y * rs;
-                    const float z2m1 = fmaf(Z2, Z2, -1.0f);
-                    gr = fmaf(Xb, k.dt, gr);
-                    float Vpb = fmaf(-0.5f * k.dt, Xb, -k.kdt * Vb);
-                    const float ub = fmaf(za, Xb, k.xi * Z2 * Vb);
-                    gk = fmaf(Vb, (k.theta - Vp) * k.dt, gk);
-                    gth = fmaf(Vb, k.kdt, gth);
-                    gxi = fmaf(Vb, fmaf(u, Z2, pos ? 0.5f * k.xi * k.dt * z2m1 : 0.0f), gxi);
-                    const float Z2b = Vb * fmaf(k.xi, u, pos ? 0.5f * k.xi * k.xi * k.dt * Z2 : 0.0f);
-                    grho = fmaf(Z2b, fmaf(-k.rho * inv_sq, zb, za), grho);
-                    Vpb = fmaf(ub, 0.5f * k.dt * rs, Vpb);           // du/dV+ = dt / (2u); 0 where u = 0
-                    Vb = pos ? Vb + Vpb : Vb;
-                }
-            }
-            g[q][0] = gS0;
-            g[q][1] = Vb;                                            // dP/dv0 = adjoint of V_0
-            g[q][2] = gk;
-            g[q][3] = gth;
-            g[q][4] = gxi;
-            g[q][5] = grho;
-            g[q][6] = fmaf(-T, sd.x, gr);                            // plus the discount factor
-            if (!keep) {
-#pragma unroll
-                for (int j = 0; j < 7; ++j) g[q][j] = 0.0f;
-            }
-        }
-        double *row = a.rows + tile * 14u;
-#pragma unroll
-        for (int j = 0; j < 7; ++j) {
-            const float sx = warp_sum(g[0][j] + g[1][j]);
-            const float sxx = warp_sum(g[0][j] * g[0][j] + g[1][j] * g[1][j]);
-            if (lane == j) row[j] = (double)sx;
-            if (lane == 7 + j) row[7 + j] = (double)sxx;
-        }
-    }
-}
-
-// Reduce tile rows of `width` columns (sums then sums of squares, E = width/2
-// estimators) in the fixed group order, writing mean[E] then se[E].
-__global__ void reduce_generic_final_kernel(const double *group_sums, uint64_t n_groups, int E,
-                                            double n_paths, double *out)
-{
-    __shared__ double tot[32];
-    const int width = 2 * E;
-    for (int col = threadIdx.x; col < width; col += blockDim.x) {
-        double acc = 0.0;
-        for (uint64_t g = 0; g < n_groups; ++g) acc += group_sums[g * width + col];
-        tot[col] = acc;
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < E; e += blockDim.x) {
-        const double mean = tot[e] / n_paths;
-        const double var = (tot[E + e] - n_paths * mean * mean) / (n_paths - 1.0);
-        out[e] = mean;
-        out[E + e] = sqrt(var > 0.0 ? var / n_paths : 0.0);
-    }
-}
 
 // ---------------------------------------------------------------------------
 // Host side
@@ -1228,6 +62,48 @@ struct DeviceGuard {
         if (switched) cudaSetDevice(prev);
     }
 };
+
+// Stream-ordered scratch of the synchronous entry points: one pool per
+// device, owned by the library, that keeps freed memory for the next call
+// (release threshold unlimited) instead of unmapping it at every
+// synchronisation as a pool with threshold 0 does.  heston_release_cached_memory
+// trims it.
+constexpr int kMaxPoolDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[kMaxPoolDevices];
+
+cudaMemPool_t scratch_pool(int dev, bool create)
+{
+    if (dev < 0 || dev >= kMaxPoolDevices) return nullptr;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pool[dev] && create) {
+        cudaMemPoolProps props;
+        std::memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        uint64_t keep = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        g_pool[dev] = pool;
+    }
+    return g_pool[dev];
+}
+
+cudaError_t scratch_alloc(void **p, size_t bytes, cudaStream_t st)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    cudaMemPool_t pool = scratch_pool(dev, true);
+    if (!pool) return cudaMallocAsync(p, bytes, st);
+    return cudaMallocFromPoolAsync(p, bytes, pool, st);
+}
 
 struct Prepared {
     ContractSet<double> cs;
@@ -2405,7 +1281,7 @@ int qmc_price_sync(const Prepared &pp, uint64_t n_paths, uint64_t seed, heston_r
     const size_t wb = qmc_ws_layout(pp.cs.n, n_paths, pp.N, pp.opt.n_shifts).total;
     const size_t ob = 12u * pp.cs.n * sizeof(double);
     char *buf = nullptr;
-    if (cudaMallocAsync((void **)&buf, tb + wb + align256(ob), st) != cudaSuccess) {
+    if (scratch_alloc((void **)&buf, tb + wb + align256(ob), st) != cudaSuccess) {
         cudaGetLastError();
         return HESTON_ERR_NOMEM;
     }
@@ -2517,7 +1393,7 @@ int heston_mc_price_greeks_ex(const heston_params *params, const heston_contract
     const size_t ws_bytes = workspace_bytes(n_contracts, n_paths);
     const size_t out_bytes = 12u * n_contracts * sizeof(double);
     void *ws = nullptr;
-    if (cudaMallocAsync(&ws, ws_bytes + align256(out_bytes), st) != cudaSuccess) {
+    if (scratch_alloc(&ws, ws_bytes + align256(out_bytes), st) != cudaSuccess) {
         cudaGetLastError();
         return HESTON_ERR_NOMEM;
     }
@@ -2603,7 +1479,7 @@ int heston_mc_debug_paths(const heston_params *params, const heston_contract *co
     const size_t rb = sizeof(double) * kRecordDoubles * count;
     const size_t eb = sizeof(double) * 6 * n_contracts * (size_t)count;
     char *buf = nullptr;
-    if (cudaMallocAsync((void **)&buf, align256(pb) + align256(rb) + align256(eb), st) != cudaSuccess) {
+    if (scratch_alloc((void **)&buf, align256(pb) + align256(rb) + align256(eb), st) != cudaSuccess) {
         cudaGetLastError();
         return HESTON_ERR_NOMEM;
     }
@@ -2759,6 +1635,21 @@ int heston_mc_adjoint_backward(const heston_params *params, const heston_contrac
 {
     return adjoint_enqueue(true, params, contract, n_paths, n_steps, rng_seed, opts, d_workspace,
                            workspace_bytes_, d_grad);
+}
+
+int heston_release_cached_memory(int32_t device)
+{
+    int lo = device, hi = device + 1;
+    if (device < 0) { lo = 0; hi = kMaxPoolDevices; }
+    if (hi > kMaxPoolDevices) return HESTON_ERR_INVALID_ARG;
+    for (int d = lo; d < hi; ++d) {
+        cudaMemPool_t pool = scratch_pool(d, false);
+        if (pool && cudaMemPoolTrimTo(pool, 0) != cudaSuccess) {
+            cudaGetLastError();
+            return HESTON_ERR_CUDA;
+        }
+    }
+    return HESTON_OK;
 }
 
 int heston_server_create(const heston_server_config *cfg, heston_server **out)

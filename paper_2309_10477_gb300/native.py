@@ -142,6 +142,7 @@ def load():
                                        P(heston_options), vp, sz, vp], i32),
         "heston_mc_adjoint_backward": ([P(heston_params), P(heston_contract), u64, u32, u64,
                                         P(heston_options), vp, sz, vp], i32),
+        "heston_release_cached_memory": ([i32], i32),
         "heston_server_create": ([P(heston_server_config), P(vp)], i32),
         "heston_server_submit": ([vp, P(heston_batch_item), P(u64)], i32),
         "heston_server_poll": ([vp, u64, P(heston_result), P(ctypes.c_double)], i32),
@@ -455,3 +456,8 @@ class HestonServer:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def heston_release_cached_memory(device: int = -1) -> None:
+    """Return the library's cached stream-ordered scratch to the driver."""
+    _check(load().heston_release_cached_memory(device))

@@ -364,3 +364,19 @@ def test_asian_with_sparse_dates_and_odd_steps(nv):
         gm, _ = _gpu_estimates(nv, PAPER, cs, 2000, N, 2, nv.HESTON_FP64)
         om, _ = oracle.mc_price_greeks(oracle.Params(**PAPER), _oc(cs), 2000, N, 2)
         np.testing.assert_allclose(gm, om, rtol=1e-9, atol=1e-11)
+
+
+def test_cached_scratch_reuse_and_release(nv):
+    """Repeated synchronous calls reuse the cached scratch and give the same
+    bits; releasing it between calls changes nothing."""
+    cs = _contracts_for(16)
+    args = (_gp(nv, BASE), _gc(nv, cs), 64 * 40 + 3, 16, 5, nv.make_options(prec=nv.HESTON_FP32))
+    ref = nv.results_to_arrays(nv.heston_mc_price_greeks_ex(*args))
+    for release in (False, True, False):
+        if release:
+            nv.heston_release_cached_memory(-1)
+            nv.heston_release_cached_memory(0)
+        got = nv.results_to_arrays(nv.heston_mc_price_greeks_ex(*args))
+        assert all(np.array_equal(a, b) for a, b in zip(ref, got))
+    with pytest.raises(nv.HestonError):
+        nv.heston_release_cached_memory(64)
