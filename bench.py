@@ -469,7 +469,7 @@ def run_gpu(args):
         arrivals = np.cumsum(g.exponential(1.0 / rate, n_req))
         reqs = [nv.make_batch_item(nv.make_params(**d["params"]), nv.make_contract(*d["contract"]),
                                    d["n_paths"], d["n_steps"], w.seed + 7919 * i)
-                for i, d in enumerate(wl.batched_contracts(n_req, seed=2309))]
+                for i, d in enumerate(wl.serving_requests(n_req, seed=2309))]
         req_path_steps = sum(it.n_paths * it.n_steps for it in reqs)
         srv = nv.HestonServer(1 << 30, tiles_per_round=args.serve_tiles_per_round, device=local)
         for t in [srv.submit(it) for it in reqs[:64]]:           # warm-up
@@ -504,6 +504,7 @@ def run_gpu(args):
                 pass
             tickets[i] = srv.submit(reqs[i])
         submit_s = time.perf_counter() - t0
+        st_mid = srv.stats()
         submitted.set()
         th_c.join()
         wall_s = time.perf_counter() - t0
@@ -513,17 +514,22 @@ def run_gpu(args):
         srv.close()
         la = np.array(lat) * 1e3
         serving = {"workload": f"Poisson arrivals at {rate:.0f}/s for {dur:.0f} s ({n_req} requests), "
-                               "each one contract drawn like the batched form (paths 2^U, U~U[14,20]; "
-                               "steps 50..500; European/Asian), FP32",
+                               "each one contract with parameters drawn like the batched form, "
+                               "paths 2^U (U~U[16,22]), steps 50..252, European/Asian, FP32",
+                   "offered_load_vs_batched_kernel": None,
                    "offered_path_steps_per_s": req_path_steps / arrivals[-1],
                    "latency_ms": {"p50": float(np.percentile(la, 50)), "p90": float(np.percentile(la, 90)),
                                   "p99": float(np.percentile(la, 99)), "max": float(la.max())},
                    "greek_sets_per_s": n_req / wall_s, "path_steps_per_s": req_path_steps / wall_s,
                    "drain_after_last_arrival_ms": (wall_s - submit_s) * 1e3,
                    "max_requests_in_system": queued_max[0],
+                   "in_system_at_last_arrival": int(st_mid.queued + st_mid.active),
                    "rounds": int(st1.rounds - st0.rounds),
                    "tiles_per_round": args.serve_tiles_per_round,
                    "memory_peak_bytes": int(st1.memory_peak)}
+        if batched is not None:
+            serving["offered_load_vs_batched_kernel"] = (serving["offered_path_steps_per_s"]
+                                                         / batched["path_steps_per_s"])
 
     # end to end through the synchronous host API (host structs in, results out)
     res_arr = (nv.heston_result * nc)()
@@ -619,8 +625,8 @@ def main():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--no-schemes", action="store_true", help="skip the Euler / QE variants")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="request arrivals per second")
-    ap.add_argument("--serve-seconds", type=float, default=5.0)
-    ap.add_argument("--serve-tiles-per-round", type=int, default=16384)
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--serve-tiles-per-round", type=int, default=65536)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--n-paths", type=int, default=0,
                     help="paths per rank (default: the workload's 2^22); small cases for ncu")

@@ -992,20 +992,21 @@ int adjoint_enqueue(bool backward, const heston_params *params, const heston_con
 struct heston_server {
     heston_server_config cfg;
     int device = 0;
-    cudaStream_t stream = nullptr;
+    cudaStream_t strm[2] = {nullptr, nullptr};   // rounds alternate between two streams
     int n_sm = 0, per_sm = 0;
     // device buffers
     BatchItemDev *d_slots = nullptr;
-    double *d_pool = nullptr, *d_groups = nullptr, *d_results = nullptr;
-    uint64_t *d_wb[2] = {nullptr, nullptr}, *d_wt[2] = {nullptr, nullptr};
-    uint32_t *d_wi[2] = {nullptr, nullptr};
-    unsigned long long *d_counter = nullptr;
+    double *d_pool = nullptr;
+    double *d_groups[2] = {nullptr, nullptr};    // group rows of the round's finishing requests
+    char *d_pack[2] = {nullptr, nullptr};        // the round's work lists (RoundLayout)
+    double *d_res[2] = {nullptr, nullptr};       // results of the finishing requests, in list order
     // pinned host staging
     BatchItemDev *h_slots = nullptr;
-    uint64_t *h_wb[2] = {nullptr, nullptr}, *h_wt[2] = {nullptr, nullptr};
-    uint32_t *h_wi[2] = {nullptr, nullptr};
-    double *h_results = nullptr;
-    cudaEvent_t ev[2] = {nullptr, nullptr};
+    char *h_pack[2] = {nullptr, nullptr};
+    double *h_res[2] = {nullptr, nullptr};
+    cudaEvent_t ev[2] = {nullptr, nullptr};      // round on buffer b done (results on the host)
+    cudaEvent_t ev_copy[2] = {nullptr, nullptr}; // round's copies done
+    cudaEvent_t ev_kern[2] = {nullptr, nullptr}; // round's path kernel done
     // host state
     struct Req {
         uint64_t ticket = 0;
@@ -1076,6 +1077,24 @@ size_t srv_req_bytes(uint64_t tiles)
     return (b + kPoolUnit - 1) / kPoolUnit * kPoolUnit;
 }
 
+// One round's work lists in a single pinned buffer (one copy per round):
+// the work counter (zero), then per position its first work index, first
+// tile and slot, then per finishing request its first group row and slot.
+struct RoundLayout {
+    size_t wb, wt, wi, fg, fs, total;
+};
+RoundLayout round_layout(size_t n, size_t nf)
+{
+    RoundLayout L;
+    L.wb = 8;
+    L.wt = L.wb + 8 * n;
+    L.wi = L.wt + 8 * n;
+    L.fg = (L.wi + 4 * n + 7) & ~(size_t)7;
+    L.fs = L.fg + 8 * nf;
+    L.total = L.fs + 4 * nf;
+    return L;
+}
+
 // Retire the requests whose reduction ran in the round on buffer b.
 void srv_retire(heston_server *s, int b)
 {
@@ -1083,11 +1102,12 @@ void srv_retire(heston_server *s, int b)
     const bool failed = cudaEventSynchronize(s->ev[b]) != cudaSuccess;
     const auto now = std::chrono::steady_clock::now();
     std::lock_guard<std::mutex> lock(s->mu);
-    for (int slot : s->pending[b]) {
+    for (size_t p = 0; p < s->pending[b].size(); ++p) {
+        const int slot = s->pending[b][p];
         heston_server::Req &r = s->slots[slot];
         heston_server::Done d;
         const bool gn = r.dev.gamma_nan != 0;
-        fill_results(s->h_results + (size_t)slot * 12u, 1, r.dev.n_paths,
+        fill_results(s->h_res[b] + p * 12u, 1, r.dev.n_paths,
                      gn ? HESTON_WARN_GAMMA_UNDEFINED : HESTON_OK, &d.res);
         if (failed) d.res.status = HESTON_ERR_CUDA;
         d.latency = std::chrono::duration<double>(now - r.t_submit).count();
@@ -1127,7 +1147,7 @@ void srv_loop(heston_server *s)
                 q.dev.row_begin = off / (12u * sizeof(double));
                 s->h_slots[slot] = q.dev;
                 cudaMemcpyAsync(s->d_slots + slot, s->h_slots + slot, sizeof(BatchItemDev),
-                                cudaMemcpyHostToDevice, s->stream);
+                                cudaMemcpyHostToDevice, s->strm[b]);
                 s->slots[slot] = q;
                 s->order.push_back((uint64_t)slot);
                 s->st.memory_in_use += q.bytes;
@@ -1151,6 +1171,17 @@ void srv_loop(heston_server *s)
                     round_tiles.push_back(take);
                     left -= take;
                 }
+                // most steps first, so that short tiles fill the end of the round
+                std::vector<size_t> idx(round_slots.size());
+                for (size_t i = 0; i < idx.size(); ++i) idx[i] = i;
+                std::stable_sort(idx.begin(), idx.end(), [&](size_t x, size_t y) {
+                    return s->slots[round_slots[x]].dev.N > s->slots[round_slots[y]].dev.N;
+                });
+                std::vector<int> rs(idx.size());
+                std::vector<uint64_t> rt(idx.size());
+                for (size_t i = 0; i < idx.size(); ++i) { rs[i] = round_slots[idx[i]]; rt[i] = round_tiles[idx[i]]; }
+                round_slots.swap(rs);
+                round_tiles.swap(rt);
             }
             const bool busy = !round_slots.empty() || !s->pending[0].empty() || !s->pending[1].empty();
             if (!busy) {
@@ -1160,51 +1191,73 @@ void srv_loop(heston_server *s)
             }
         }
         if (!round_slots.empty()) {
-            // buffer b was last used two rounds ago: its copies and kernels are done
+            // buffer b was last used two rounds ago: wait for that round, retire it
             srv_retire(s, b);
             cudaEventSynchronize(s->ev[b]);
+            cudaStream_t st = s->strm[b];
             const uint32_t n = (uint32_t)round_slots.size();
             uint64_t acc = 0;
             for (uint32_t p = 0; p < n; ++p) {
                 heston_server::Req &r = s->slots[round_slots[p]];
-                s->h_wb[b][p] = acc;
-                s->h_wi[b][p] = (uint32_t)round_slots[p];
-                s->h_wt[b][p] = r.next_tile;
-                acc += round_tiles[p];
                 r.next_tile += round_tiles[p];
                 if (r.next_tile == r.tiles) finishing.push_back(round_slots[p]);
             }
-            cudaMemcpyAsync(s->d_wb[b], s->h_wb[b], n * sizeof(uint64_t), cudaMemcpyHostToDevice, s->stream);
-            cudaMemcpyAsync(s->d_wi[b], s->h_wi[b], n * sizeof(uint32_t), cudaMemcpyHostToDevice, s->stream);
-            cudaMemcpyAsync(s->d_wt[b], s->h_wt[b], n * sizeof(uint64_t), cudaMemcpyHostToDevice, s->stream);
-            cudaMemsetAsync(s->d_counter, 0, sizeof(unsigned long long), s->stream);
+            const uint32_t nf = (uint32_t)finishing.size();
+            const RoundLayout L = round_layout(n, nf);
+            char *hp = s->h_pack[b], *dp = s->d_pack[b];
+            *(uint64_t *)hp = 0;
+            uint64_t *hwb = (uint64_t *)(hp + L.wb), *hwt = (uint64_t *)(hp + L.wt);
+            uint32_t *hwi = (uint32_t *)(hp + L.wi);
+            for (uint32_t p = 0; p < n; ++p) {
+                const heston_server::Req &r = s->slots[round_slots[p]];
+                hwb[p] = acc;
+                hwt[p] = r.next_tile - round_tiles[p];
+                hwi[p] = (uint32_t)round_slots[p];
+                acc += round_tiles[p];
+            }
+            uint64_t gacc = 0;
+            uint64_t *hfg = (uint64_t *)(hp + L.fg);
+            uint32_t *hfs = (uint32_t *)(hp + L.fs);
+            for (uint32_t p = 0; p < nf; ++p) {
+                hfs[p] = (uint32_t)finishing[p];
+                hfg[p] = gacc;
+                gacc += groups_for(s->slots[finishing[p]].tiles);
+            }
+            cudaMemcpyAsync(dp, hp, L.total, cudaMemcpyHostToDevice, st);
+            // descriptors admitted for the previous round were copied on the other stream
+            cudaStreamWaitEvent(st, s->ev_copy[1 - b], 0);
+            cudaEventRecord(s->ev_copy[b], st);
             BatchLaunch a;
             a.items = s->d_slots;
-            a.work_begin = s->d_wb[b];
-            a.work_item = s->d_wi[b];
-            a.work_tile0 = s->d_wt[b];
+            a.work_begin = (const uint64_t *)(dp + L.wb);
+            a.work_item = (const uint32_t *)(dp + L.wi);
+            a.work_tile0 = (const uint64_t *)(dp + L.wt);
             a.group_begin = nullptr;
             a.n_items = n;
             a.total_work = acc;
-            a.counter = s->d_counter;
+            a.counter = (unsigned long long *)dp;
             a.status = nullptr;
             a.rows = s->d_pool;
             const uint64_t grid = std::min<uint64_t>((acc + 3) / 4, (uint64_t)s->n_sm * s->per_sm);
             if (s->cfg.trunc == HESTON_TRUNC_FULL)
-                heston_batch_kernel<0><<<(unsigned)std::max<uint64_t>(grid, 1), kPathBlock, 0, s->stream>>>(a);
+                heston_batch_kernel<0><<<(unsigned)std::max<uint64_t>(grid, 1), kPathBlock, 0, st>>>(a);
             else
-                heston_batch_kernel<1><<<(unsigned)std::max<uint64_t>(grid, 1), kPathBlock, 0, s->stream>>>(a);
-            for (int slot : finishing) {
-                const heston_server::Req &r = s->slots[slot];
-                const double *rows = s->d_pool + r.dev.row_begin * 12u;
-                const uint64_t ng = groups_for(r.tiles);
-                reduce_groups_kernel<<<(unsigned)ng, 64, 0, s->stream>>>(rows, r.tiles, 12, s->d_groups);
-                reduce_final_kernel<<<1, 64, 0, s->stream>>>(s->d_groups, ng, 1, (double)r.dev.n_paths,
-                                                             r.dev.gamma_nan, s->d_results + (size_t)slot * 12u);
-                cudaMemcpyAsync(s->h_results + (size_t)slot * 12u, s->d_results + (size_t)slot * 12u,
-                                12u * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+                heston_batch_kernel<1><<<(unsigned)std::max<uint64_t>(grid, 1), kPathBlock, 0, st>>>(a);
+            cudaEventRecord(s->ev_kern[b], st);
+            // the requests that finished: one reduction launch per level for all of them,
+            // after the previous round's tiles (other stream) too
+            if (nf) {
+                cudaStreamWaitEvent(st, s->ev_kern[1 - b], 0);
+                server_reduce_groups_kernel<<<(unsigned)gacc, 64, 0, st>>>(
+                    s->d_slots, (const uint32_t *)(dp + L.fs), (const uint64_t *)(dp + L.fg), nf, s->d_pool,
+                    s->d_groups[b]);
+                server_reduce_final_kernel<<<nf, 64, 0, st>>>(s->d_slots, (const uint32_t *)(dp + L.fs),
+                                                              (const uint64_t *)(dp + L.fg), s->d_groups[b],
+                                                              s->d_res[b]);
+                cudaMemcpyAsync(s->h_res[b], s->d_res[b], (size_t)nf * 12u * sizeof(double),
+                                cudaMemcpyDeviceToHost, st);
             }
-            cudaEventRecord(s->ev[b], s->stream);
+            cudaEventRecord(s->ev[b], st);
             {
                 std::lock_guard<std::mutex> lock(s->mu);
                 s->pending[b] = finishing;
@@ -1223,15 +1276,16 @@ void srv_loop(heston_server *s)
 
 void srv_free_buffers(heston_server *s)
 {
-    cudaFree(s->d_slots); cudaFree(s->d_pool); cudaFree(s->d_groups); cudaFree(s->d_results);
-    cudaFree(s->d_counter);
+    cudaFree(s->d_slots); cudaFree(s->d_pool);
     for (int b = 0; b < 2; ++b) {
-        cudaFree(s->d_wb[b]); cudaFree(s->d_wi[b]); cudaFree(s->d_wt[b]);
-        cudaFreeHost(s->h_wb[b]); cudaFreeHost(s->h_wi[b]); cudaFreeHost(s->h_wt[b]);
+        cudaFree(s->d_groups[b]); cudaFree(s->d_pack[b]); cudaFree(s->d_res[b]);
+        cudaFreeHost(s->h_pack[b]); cudaFreeHost(s->h_res[b]);
         if (s->ev[b]) cudaEventDestroy(s->ev[b]);
+        if (s->ev_copy[b]) cudaEventDestroy(s->ev_copy[b]);
+        if (s->ev_kern[b]) cudaEventDestroy(s->ev_kern[b]);
+        if (s->strm[b]) cudaStreamDestroy(s->strm[b]);
     }
-    cudaFreeHost(s->h_slots); cudaFreeHost(s->h_results);
-    if (s->stream) cudaStreamDestroy(s->stream);
+    cudaFreeHost(s->h_slots);
 }
 
 }  // namespace
@@ -1667,24 +1721,29 @@ int heston_server_create(const heston_server_config *cfg, heston_server **out)
     e |= (int)cudaDeviceGetAttribute(&s->n_sm, cudaDevAttrMultiProcessorCount, s->device);
     e |= (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s->per_sm, heston_batch_kernel<0>, kPathBlock, 0);
     if (s->per_sm < 1) s->per_sm = 1;
-    e |= (int)cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
     s->pool_bytes = cfg->memory_bytes / kPoolUnit * kPoolUnit;
     e |= (int)cudaMalloc((void **)&s->d_slots, S * sizeof(BatchItemDev));
     e |= (int)cudaMalloc((void **)&s->d_pool, s->pool_bytes);
-    e |= (int)cudaMalloc((void **)&s->d_groups, (size_t)groups_for(s->pool_bytes / 96 + 1) * 12 * sizeof(double) + 256);
-    e |= (int)cudaMalloc((void **)&s->d_results, (size_t)S * 12 * sizeof(double));
-    e |= (int)cudaMalloc((void **)&s->d_counter, 256);
     e |= (int)cudaHostAlloc((void **)&s->h_slots, S * sizeof(BatchItemDev), cudaHostAllocDefault);
-    e |= (int)cudaHostAlloc((void **)&s->h_results, (size_t)S * 12 * sizeof(double), cudaHostAllocDefault);
+    // group rows of one round's finishing requests: at most one partial group each beyond
+    // the whole groups of the pool
+    const size_t group_bytes = ((size_t)groups_for(s->pool_bytes / 96 + 1) + S) * 12 * sizeof(double);
+    const size_t pack_bytes = round_layout(S, S).total;
     for (int b = 0; b < 2; ++b) {
-        e |= (int)cudaMalloc((void **)&s->d_wb[b], S * sizeof(uint64_t));
-        e |= (int)cudaMalloc((void **)&s->d_wi[b], S * sizeof(uint32_t));
-        e |= (int)cudaMalloc((void **)&s->d_wt[b], S * sizeof(uint64_t));
-        e |= (int)cudaHostAlloc((void **)&s->h_wb[b], S * sizeof(uint64_t), cudaHostAllocDefault);
-        e |= (int)cudaHostAlloc((void **)&s->h_wi[b], S * sizeof(uint32_t), cudaHostAllocDefault);
-        e |= (int)cudaHostAlloc((void **)&s->h_wt[b], S * sizeof(uint64_t), cudaHostAllocDefault);
+        e |= (int)cudaStreamCreateWithFlags(&s->strm[b], cudaStreamNonBlocking);
+        e |= (int)cudaMalloc((void **)&s->d_groups[b], group_bytes);
+        e |= (int)cudaMalloc((void **)&s->d_pack[b], pack_bytes);
+        e |= (int)cudaMalloc((void **)&s->d_res[b], (size_t)S * 12 * sizeof(double));
+        e |= (int)cudaHostAlloc((void **)&s->h_pack[b], pack_bytes, cudaHostAllocDefault);
+        e |= (int)cudaHostAlloc((void **)&s->h_res[b], (size_t)S * 12 * sizeof(double), cudaHostAllocDefault);
         e |= (int)cudaEventCreateWithFlags(&s->ev[b], cudaEventDisableTiming);
-        cudaEventRecord(s->ev[b], s->stream);
+        e |= (int)cudaEventCreateWithFlags(&s->ev_copy[b], cudaEventDisableTiming);
+        e |= (int)cudaEventCreateWithFlags(&s->ev_kern[b], cudaEventDisableTiming);
+    }
+    for (int b = 0; b < 2 && e == 0; ++b) {
+        cudaEventRecord(s->ev[b], s->strm[b]);
+        cudaEventRecord(s->ev_copy[b], s->strm[b]);
+        cudaEventRecord(s->ev_kern[b], s->strm[b]);
     }
     if (e != 0) {
         cudaGetLastError();
@@ -1769,7 +1828,8 @@ int heston_server_destroy(heston_server *s)
     }
     s->cv_work.notify_all();
     if (s->th.joinable()) s->th.join();
-    cudaStreamSynchronize(s->stream);
+    cudaStreamSynchronize(s->strm[0]);
+    cudaStreamSynchronize(s->strm[1]);
     srv_free_buffers(s);
     delete s;
     return HESTON_OK;

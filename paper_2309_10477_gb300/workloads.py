@@ -74,3 +74,16 @@ def batched_contracts(n: int = 1024, seed: int = 42):
         out.append(dict(params=p, contract=(payoff, K, T, 0, 0), n_paths=max(n_paths, 256),
                         n_steps=n_steps))
     return out
+
+
+def serving_requests(n: int, seed: int = 2309):
+    """Serving stream requests: contracts drawn as in batched_contracts (same
+    parameter and contract distributions), paths 2^U with U~U[16,22] rounded
+    to 256, steps U{50..252}.  Returns a list of dicts like batched_contracts."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for d in batched_contracts(n, seed=seed + 1):
+        n_paths = int(round(2.0 ** g.uniform(16.0, 22.0) / 256.0)) * 256
+        d = dict(d, n_paths=max(n_paths, 256), n_steps=int(g.integers(50, 253)))
+        out.append(d)
+    return out
