@@ -511,7 +511,32 @@ def run_gpu(args):
         th_w.join()
         clocks.mark(False)
         st1 = srv.stats()
+        # capacity: 2000 requests of the same stream submitted at once, against the
+        # same requests launched one per contract (same paths, hence the same SE)
+        creqs = [nv.make_batch_item(nv.make_params(**d["params"]), nv.make_contract(*d["contract"]),
+                                    d["n_paths"], d["n_steps"], w.seed + 104729 * i)
+                 for i, d in enumerate(wl.serving_requests(2000, seed=77))]
+        torch.cuda.synchronize()
+        t_c = time.perf_counter()
+        ctk = [srv.submit(it) for it in creqs]
+        cres = [srv.wait(t, 120000) for t in ctk]
+        cap_s = time.perf_counter() - t_c
         srv.close()
+        max_np = max(it.n_paths for it in creqs)
+        cws_bytes = nv.heston_mc_workspace_bytes(1, max_np)
+        cws = torch.empty(cws_bytes // 8 + 32, dtype=torch.float64, device=dev)
+        cout = torch.empty(len(creqs) * 12, dtype=torch.float64, device=dev)
+        copts = nv.make_options(prec=nv.HESTON_FP32, stream=stream, device=local)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i, it in enumerate(creqs):
+            nv.heston_mc_launch(it.params, [it.contract], it.n_paths, it.n_steps, it.rng_seed, copts,
+                                cws, nv.heston_mc_workspace_bytes(1, it.n_paths), cout[i * 12:(i + 1) * 12])
+        e1.record(stream)
+        e1.synchronize()
+        pc_s = e0.elapsed_time(e1) * 1e-3
+        cgot = np.array([[getattr(r, k) for k in nv.ESTIMATORS] + list(r.se) for r, _ in cres])
+        csame = bool(np.array_equal(np.nan_to_num(cgot), np.nan_to_num(cout.view(-1, 12).cpu().numpy())))
         la = np.array(lat) * 1e3
         serving = {"workload": f"Poisson arrivals at {rate:.0f}/s for {dur:.0f} s ({n_req} requests), "
                                "each one contract with parameters drawn like the batched form, "
@@ -526,7 +551,13 @@ def run_gpu(args):
                    "in_system_at_last_arrival": int(st_mid.queued + st_mid.active),
                    "rounds": int(st1.rounds - st0.rounds),
                    "tiles_per_round": args.serve_tiles_per_round,
-                   "memory_peak_bytes": int(st1.memory_peak)}
+                   "memory_peak_bytes": int(st1.memory_peak),
+                   "saturated": {"requests": len(creqs), "greek_sets_per_s": len(creqs) / cap_s,
+                                 "per_contract_greek_sets_per_s": len(creqs) / pc_s,
+                                 "speedup_vs_per_contract": pc_s / cap_s,
+                                 "results_identical_to_per_contract": csame,
+                                 "note": "served: host wall time from first submit to last result; "
+                                         "per-contract: CUDA events around 2000 heston_mc_launch calls"}}
         if batched is not None:
             serving["offered_load_vs_batched_kernel"] = (serving["offered_path_steps_per_s"]
                                                          / batched["path_steps_per_s"])
