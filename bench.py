@@ -33,13 +33,20 @@ sys.path.insert(0, ROOT)
 METRIC = "path-steps/s at fixed std error (Greek-sets/s alongside)"
 UNIT = "path-steps/s"
 
-# Algorithmic thread-instructions per path-step for this workload (FP32 path,
-# full truncation, European + Asian with a date every step, Vega/Theta
-# tangents, Gamma weights): Philox4x32-10 half call 30, uniforms 6,
-# Box-Muller 9 (4 MUFU), correlation 4, truncation + sqrt 8, tangent du 5,
-# Gamma weights 2, ln S step 3, ln S tangents 5, V step 8, V tangents 10,
-# Asian date 7 (1 MUFU), loop 1.  Total 98, of which 6 on the MUFU pipe.
-ALGO_INSTR_PER_PATH_STEP = 98
+# Algorithmic work per path-step for this workload (FP32 path, full
+# truncation, European + Asian with a date every step, Vega/Theta tangents,
+# Gamma weights), counted from the operations the method needs:
+#   88 scalar operations.  40 cannot pack: Philox4x32-10 half block 20 (10
+#   rounds x 2 wide multiplies + 2 three-way xors, per 2 steps; the round keys
+#   are loop-invariant), uniform masks + conversions 4, Box-Muller
+#   lg2/sqrt/sin/cos 4 + branch select 2, truncation compare/max/selects 5 +
+#   rsqrt 1, Milstein-term selects 2, Asian ex2 1, loop 1.  48 are FP32 adds /
+#   multiplies / FMAs (uniform scaling 2, Box-Muller 9, step 32, Asian date 5),
+#   which sm_100's f32x2 instructions retire two per issue slot.
+# The issue-slot ceiling is therefore 40 + 48/2 = 64 thread-instruction slots
+# per path-step against 1 slot per lane per clock.
+ALGO_OPS_PER_PATH_STEP = 88
+ALGO_SLOTS_PER_PATH_STEP = 64
 ISSUE_LANES_PER_SM_CLK = 128          # 4 SM sub-partitions x 1 warp-instruction x 32 lanes
 FLUSH_BYTES = 256 << 20               # > 129 MB L2
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "heston_paths_kernel_multi_strike_2p22.md")
@@ -593,7 +600,7 @@ def run_gpu(args):
         clk = clocks.summary()
         max_mhz = float(peaks.get("sm_max_mhz") or clk.get("sm_max_mhz") or 2070.0)
         peak_tinst = n_sm * ISSUE_LANES_PER_SM_CLK * max_mhz * 1e6 / 1e12
-        achieved_tinst = path_steps * ALGO_INSTR_PER_PATH_STEP / (k1 * 1e-3) / 1e12
+        achieved_tinst = path_steps * ALGO_SLOTS_PER_PATH_STEP / (k1 * 1e-3) / 1e12
         traffic = _profiled_traffic()
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -617,8 +624,11 @@ def run_gpu(args):
             "gpu_launches": 3 * args.steps,
             "roofline": {"bound": "alu", "kernel": "heston_paths_kernel<float,FULL,ASIAN>",
                          "achieved": achieved_tinst, "peak": peak_tinst,
-                         "unit": f"T thread-instr/s ({ALGO_INSTR_PER_PATH_STEP} algorithmic per "
-                                 f"path-step; peak = {n_sm} SMs x 128 lanes x {max_mhz:.0f} MHz)",
+                         "unit": f"T issue slots/s ({ALGO_SLOTS_PER_PATH_STEP} algorithmic slots per "
+                                 f"path-step: {ALGO_OPS_PER_PATH_STEP} operations, FP32 ones packed "
+                                 f"two per f32x2 instruction; peak = {n_sm} SMs x 128 lanes x "
+                                 f"{max_mhz:.0f} MHz)",
+                         "ops_per_s": path_steps * ALGO_OPS_PER_PATH_STEP / (k1 * 1e-3) / 1e12,
                          "frac": achieved_tinst / peak_tinst, "traffic": traffic,
                          "kernel_ms": k1,
                          "path_steps_per_s_kernel": path_steps / (k1 * 1e-3)},

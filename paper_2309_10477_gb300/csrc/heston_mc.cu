@@ -234,6 +234,12 @@ int validate_and_prepare(const heston_params *p, const heston_contract *c, uint3
     kd.sq = sq;
     kd.kappa = p->kappa;
     kd.theta = p->theta;
+    kd.xrho = p->xi * p->rho;
+    kd.xsq = p->xi * sq;
+    kd.xi2 = p->xi * p->xi;
+    kd.qdt = 0.25 * dt;
+    kd.qddt = 0.25 * ddt;
+    kd.half_invT = 0.5 / T;
     // QE constants (zero unless the scheme is QE, which has kappa, theta, xi > 0)
     if (o.scheme == HESTON_SCHEME_QE) {
         const double kap = p->kappa, th = p->theta, xi2 = p->xi * p->xi;

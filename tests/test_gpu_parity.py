@@ -5,7 +5,7 @@ Tolerances:
     1e-14; FP32 normals within 1e-7 + 1.5e-6 R (R = sqrt(Za^2 + Zb^2)): the
     documented bounds of sqrt.approx (2^-22 relative), lg2.approx (2^-22
     absolute, used only where R >= 0.46, giving |dR| <= 3.6e-7) or the
-    near-1 series (1.4e-8 relative), and sin/cos.approx (2^-20.9 absolute on
+    near-1 polynomial (8.4e-9 relative), and sin/cos.approx (2^-20.9 absolute on
     [-pi, pi]) give about 9e-7 R + 3.6e-7 at the switch.
   * per path, FP64 path: every record field and estimator within 1e-9
     relative (libm rounding only).
@@ -380,3 +380,59 @@ def test_cached_scratch_reuse_and_release(nv):
         assert all(np.array_equal(a, b) for a, b in zip(ref, got))
     with pytest.raises(nv.HestonError):
         nv.heston_release_cached_memory(64)
+
+
+def _round_exact(q, bits):
+    """Round the exact rational q to the nearest float with `bits` significant
+    bits (ties to even): the rounding of one IEEE add, multiply or fma."""
+    from fractions import Fraction
+    if q == 0:
+        return 0.0
+    sign = -1 if q < 0 else 1
+    q = abs(Fraction(q))
+    e = q.numerator.bit_length() - q.denominator.bit_length()
+    if Fraction(2) ** e > q:
+        e -= 1
+    scaled = q / Fraction(2) ** (e - bits + 1)          # in [2^(bits-1), 2^bits)
+    m, r = divmod(scaled.numerator, scaled.denominator)
+    if 2 * r > scaled.denominator or (2 * r == scaled.denominator and m % 2 == 1):
+        m += 1
+    return sign * float(Fraction(m) * Fraction(2) ** (e - bits + 1))
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_tile_rows_are_the_sums_of_the_per_path_records(nv, torch_cuda, prec):
+    """The production path kernel and the per-path record kernel (the one the
+    per-path parity tests check against the oracle) compute the same paths:
+    each tile row equals, bit for bit, the warp's sums of the per-path
+    estimators -- lane l adds paths l and l + 32 of the tile (x0 + x1 and
+    fma(x0, x0, x1 * x1), zero past the last path), then a xor butterfly over
+    offsets 16, 8, 4, 2, 1 -- rounded in the path precision."""
+    from fractions import Fraction
+    torch = torch_cuda
+    bits = 24 if prec == "fp32" else 53
+    cs = _contracts_for(30)
+    nc = len(cs)
+    n, N, seed = 64 * 3 + 19, 30, 5
+    opts = nv.make_options(prec=_prec(nv, prec), stream=torch.cuda.current_stream())
+    n_tiles = -(-n // 64)
+    rows = torch.zeros(n_tiles * 12 * nc, dtype=torch.float64, device="cuda")
+    nv.heston_mc_launch_tiles(_gp(nv, BASE), _gc(nv, cs), 0, n, N, seed, opts, rows)
+    torch.cuda.synchronize()
+    rows = rows.cpu().numpy().reshape(n_tiles, 12 * nc)
+    _, est = nv.heston_mc_debug_paths(_gp(nv, BASE), _gc(nv, cs), N, seed,
+                                      nv.make_options(prec=_prec(nv, prec)),
+                                      np.arange(n, dtype=np.uint64))
+    rnd = lambda q: _round_exact(q, bits)
+    for t in range(n_tiles):
+        for c in range(nc):
+            for j in range(6):
+                x = [est[t * 64 + i, c, j] if t * 64 + i < n else 0.0 for i in range(64)]
+                sx = [rnd(Fraction(x[l]) + Fraction(x[l + 32])) for l in range(32)]
+                sxx = [rnd(Fraction(x[l]) ** 2 + Fraction(rnd(Fraction(x[l + 32]) ** 2)))
+                       for l in range(32)]
+                for o in (16, 8, 4, 2, 1):
+                    sx = [rnd(Fraction(sx[l]) + Fraction(sx[l ^ o])) for l in range(32)]
+                    sxx = [rnd(Fraction(sxx[l]) + Fraction(sxx[l ^ o])) for l in range(32)]
+                assert rows[t, c * 6 + j] == sx[0], (t, c, j)
+                assert rows[t, 6 * nc + c * 6 + j] == sxx[0], (t, c, j)

@@ -89,7 +89,15 @@ def test_per_path_fp32(nv, name, scheme, trunc, pname, params, N):
     rec_g, est_g = nv.heston_mc_debug_paths(_gp(nv, params), _gc(nv, CS), N, 42, opts, paths)
     rec_o, est_o = oracle.debug_paths(oracle.Params(**params), _oc(CS), paths, N, 42, trunc, scheme)
     vs = max(params["theta"], params["v0"])
-    flips = (rec_o[:, 14] < 1e-5 * vs) | _near_strike(rec_o, CS, params["S0"], N, 2e-5)
+    # Paths near a branch decision are counted, not compared.  Euler: within
+    # eps of V = 0, sqrt(V) turns an FP32 rounding error d in V into an error of
+    # about xi sqrt(dt) d |Z| / (2 sqrt(eps)) in the next variance step; with
+    # the paper's xi = 0.61, dt = 1/128, d ~ 2e-9 and |Z| ~ 3 that passes the
+    # 1e-5 * vs tolerance for eps below about 4e-5 vs, so the band is 1e-4 vs.
+    # QE's field is the distance of its branch switches (psi = 1.5, the zero
+    # mass), which no square root of V amplifies: 1e-5 vs.
+    band = 1e-5 if scheme == nv.HESTON_SCHEME_QE else 1e-4
+    flips = (rec_o[:, 14] < band * vs) | _near_strike(rec_o, CS, params["S0"], N, 2e-5)
     assert flips.sum() <= max(2, 0.03 * len(paths)), flips.sum()
     ok = ~flips
     X_g, X_o = rec_g[ok, 0], rec_o[ok, 0]
