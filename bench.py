@@ -322,7 +322,7 @@ def run_gpu(args):
         q_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in qev)
         qest = qout.view(nc, 12).cpu().numpy()
         se_ratio = float(qest[1, 6] / estimates[1, 6])          # price SE, European K=100
-        qmc = {"rng": "sobol+brownian-bridge, 32 digital shifts x 2^17 points",
+        qmc = {"rng": f"sobol+brownian-bridge, {R} digital shifts x {n // R} points",
                "ms_per_step": q_ms, "path_steps_per_s": n * w.n_steps / (q_ms * 1e-3),
                "price_se_k100_euro": float(qest[1, 6]), "se_ratio_vs_philox": se_ratio,
                "path_steps_per_s_at_philox_se": n * w.n_steps / (q_ms * 1e-3) / se_ratio**2,
@@ -365,7 +365,7 @@ def run_gpu(args):
         from paper_2309_10477_gb300 import autotune
         bitems = [nv.make_batch_item(nv.make_params(**d["params"]), nv.make_contract(*d["contract"]),
                                      d["n_paths"], d["n_steps"], w.seed + 1000003 * i)
-                  for i, d in enumerate(wl.batched_contracts(1024))]
+                  for i, d in enumerate(wl.batched_contracts(1024)[:args.batch_contracts])]
         bopts = nv.make_options(prec=nv.HESTON_FP32, stream=stream, device=local)
         plan = nv.heston_batch_plan_make(bitems, bopts)
         desc = torch.empty(plan.descriptor_bytes // 8 + 32, dtype=torch.float64, device=dev)
@@ -415,7 +415,16 @@ def run_gpu(args):
         single_ms = e0.elapsed_time(e1) / 2
         same = bool(torch.equal(torch.nan_to_num(bout), torch.nan_to_num(sout)))
         n_unstable = int((~torch.isfinite(bout.view(-1, 12)[:, [3, 5, 9, 11]])).any(dim=1).sum())
-        batched = {"workload": "1024 seeded uneven contracts: K~U[70,130], T in {0.25,0.5,1,2}, "
+        # roofline of the persistent kernel: algorithmic issue slots per path-step as for the
+        # path kernel (64 with a date every step), less the Asian date (1 + 5/2) where absent
+        slots = sum(it.n_paths * it.n_steps * (ALGO_SLOTS_PER_PATH_STEP - 3.5 * (
+            1.0 - (min(it.contract.n_monitor or it.n_steps, it.n_steps) / it.n_steps
+                   if it.contract.payoff == nv.HESTON_ASIAN_ARITH else 0.0))) for it in bitems)
+        n_sm_b = torch.cuda.get_device_properties(dev).multi_processor_count
+        max_mhz_b = float(_measured_peaks().get("sm_max_mhz") or 2070.0)
+        peak_b = n_sm_b * ISSUE_LANES_PER_SM_CLK * max_mhz_b * 1e6 / 1e12
+        ach_b = slots / (batch_ms * 1e-3) / 1e12
+        batched = {"workload": f"{len(bitems)} seeded uneven contracts: K~U[70,130], T in {{0.25,0.5,1,2}}, "
                                "paths 2^U (U~U[14,20]), steps 50..500, European/Asian 50/50, FP32",
                    "total_path_steps": int(plan.total_path_steps),
                    "batch_ms": batch_ms, "greek_sets_per_s": len(bitems) / (batch_ms * 1e-3),
@@ -427,7 +436,12 @@ def run_gpu(args):
                    "contracts_with_unstable_vega_theta": n_unstable,
                    "launch_shape": {"block_threads": blk, "grid_ctas": grd,
                                     "tuned_candidates": len(tune_ms)},
-                   "graph": "memset + persistent kernel + 2 reductions captured, replayed"}
+                   "graph": "memset + persistent kernel + 2 reductions captured, replayed",
+                   "roofline": {"bound": "alu", "kernel": "heston_batch_kernel<FULL> (graph replay)",
+                                "achieved": ach_b, "peak": peak_b,
+                                "unit": "T issue slots/s (64 per path-step with an Asian date every "
+                                        "step, 60.5 without; peak as for the path kernel)",
+                                "frac": ach_b / peak_b}}
 
     # adjoint gradient: 252-step Asian call, 2^20 paths, d price / d (S0, v0, kappa, theta, xi, rho, r)
     adjoint = None
@@ -665,6 +679,8 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint gradient")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--no-schemes", action="store_true", help="skip the Euler / QE variants")
+    ap.add_argument("--batch-contracts", type=int, default=1024,
+                    help="contracts in the batched mix (the first n of the seeded 1024)")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="request arrivals per second")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--serve-tiles-per-round", type=int, default=65536)
