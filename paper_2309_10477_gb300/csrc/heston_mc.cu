@@ -935,14 +935,20 @@ cudaError_t launch_adj_t(bool backward, const Prepared &pp, const AdjLaunch &a, 
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    if (backward) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, heston_adj_bwd_kernel<MON>, kPathBlock, 0);
+    const bool small = a.C <= 16u;
+    if (backward) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                      &per_sm, small ? heston_adj_bwd_kernel<MON, 16> : heston_adj_bwd_kernel<MON, kAdjMaxSeg>,
+                      kPathBlock, 0);
     else          e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, heston_adj_fwd_kernel<MON>, kPathBlock, 0);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     uint64_t grid = std::min<uint64_t>((a.n_tiles + 3) / 4, (uint64_t)n_sm * per_sm);
     if (pp.opt.grid_ctas) grid = pp.opt.grid_ctas;
     if (grid < 1) grid = 1;
-    if (backward) heston_adj_bwd_kernel<MON><<<(unsigned)grid, kPathBlock, 0, st>>>(pp.kf, pp.csf, a, (float)pp.cs.T);
+    if (backward && small)
+        heston_adj_bwd_kernel<MON, 16><<<(unsigned)grid, kPathBlock, 0, st>>>(pp.kf, pp.csf, a, (float)pp.cs.T);
+    else if (backward)
+        heston_adj_bwd_kernel<MON, kAdjMaxSeg><<<(unsigned)grid, kPathBlock, 0, st>>>(pp.kf, pp.csf, a, (float)pp.cs.T);
     else          heston_adj_fwd_kernel<MON><<<(unsigned)grid, kPathBlock, 0, st>>>(pp.kf, pp.csf, a);
     return cudaGetLastError();
 }
