@@ -654,17 +654,24 @@ template <int TRUNC, int MON>
 cudaError_t launch_qmc_t(const Prepared &pp, const QmcLaunch &a, cudaStream_t st)
 {
     auto kern = heston_qmc_kernel<TRUNC, MON>;
+    const int block = pp.opt.block_threads ? (int)pp.opt.block_threads : kPathBlock;
+    // the bridge plan and one row of D high-bit words per warp in shared memory
+    const size_t smem = (size_t)a.n_ev * sizeof(BridgeOp) + (size_t)((a.N + 4u) & ~3u) * sizeof(int32_t)
+                        + (size_t)(block / 32) * a.D * sizeof(uint32_t);
     int dev = 0, n_sm = 0, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPathBlock, 0);
+    if (e == cudaSuccess && smem > 48 * 1024)
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
+    const uint64_t warps_per_cta = (uint64_t)block / 32;
     uint64_t grid = pp.opt.grid_ctas ? pp.opt.grid_ctas
-                                     : std::min<uint64_t>((a.n_tiles + 3) / 4, (uint64_t)n_sm * per_sm);
+                                     : std::min<uint64_t>((a.n_tiles + warps_per_cta - 1) / warps_per_cta,
+                                                          (uint64_t)n_sm * per_sm);
     if (grid < 1) grid = 1;
-    const int block = pp.opt.block_threads ? (int)pp.opt.block_threads : kPathBlock;
-    kern<<<(unsigned)grid, block, 0, st>>>(pp.kf, pp.csf, a);
+    kern<<<(unsigned)grid, block, smem, st>>>(pp.kf, pp.csf, a);
     return cudaGetLastError();
 }
 
@@ -681,6 +688,7 @@ int enqueue_qmc(const Prepared &pp, uint64_t n_paths, uint64_t seed, const void 
     char *b = (char *)ws;
     QmcLaunch a;
     a.tb = qmc_tables_at(d_tables, TL);
+    a.n_ev = (uint32_t)plan.ev.size();
     a.D = 2u * pp.N;
     a.N = pp.N;
     a.n_tiles = tiles_for(n_paths);
