@@ -23,6 +23,7 @@ import numpy as np
 import pytest
 
 import oracle
+from exact_rounding import round_exact
 from paper_2309_10477_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
@@ -382,24 +383,6 @@ def test_cached_scratch_reuse_and_release(nv):
         nv.heston_release_cached_memory(64)
 
 
-def _round_exact(q, bits):
-    """Round the exact rational q to the nearest float with `bits` significant
-    bits (ties to even): the rounding of one IEEE add, multiply or fma."""
-    from fractions import Fraction
-    if q == 0:
-        return 0.0
-    sign = -1 if q < 0 else 1
-    q = abs(Fraction(q))
-    e = q.numerator.bit_length() - q.denominator.bit_length()
-    if Fraction(2) ** e > q:
-        e -= 1
-    scaled = q / Fraction(2) ** (e - bits + 1)          # in [2^(bits-1), 2^bits)
-    m, r = divmod(scaled.numerator, scaled.denominator)
-    if 2 * r > scaled.denominator or (2 * r == scaled.denominator and m % 2 == 1):
-        m += 1
-    return sign * float(Fraction(m) * Fraction(2) ** (e - bits + 1))
-
-
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
 def test_tile_rows_are_the_sums_of_the_per_path_records(nv, torch_cuda, prec):
     """The production path kernel and the per-path record kernel (the one the
@@ -423,7 +406,7 @@ def test_tile_rows_are_the_sums_of_the_per_path_records(nv, torch_cuda, prec):
     _, est = nv.heston_mc_debug_paths(_gp(nv, BASE), _gc(nv, cs), N, seed,
                                       nv.make_options(prec=_prec(nv, prec)),
                                       np.arange(n, dtype=np.uint64))
-    rnd = lambda q: _round_exact(q, bits)
+    rnd = lambda q: round_exact(q, bits)
     for t in range(n_tiles):
         for c in range(nc):
             for j in range(6):

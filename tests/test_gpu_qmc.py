@@ -116,3 +116,40 @@ def test_qmc_rejections(nv):
             nv.heston_mc_price_greeks_ex(p, cs, n_paths, 16, 1, nv.make_options(
                 prec=nv.HESTON_FP32, rng=nv.HESTON_RNG_SOBOL_BB, n_shifts=n_shifts))
         assert e.value.status == nv.HESTON_ERR_INVALID_ARG
+
+
+def test_qmc_estimates_are_the_sums_of_the_per_path_records(nv):
+    """The QMC path kernel (two paths per lane, packed FP32 step) and the QMC
+    per-path record kernel (one path per thread, scalar step; the one the
+    per-path test above checks against the oracle) compute the same paths:
+    the launch's estimates equal those rebuilt on the host from the per-path
+    records -- exactly rounded FP32 tile sums (lane l adds points l and
+    l + 32 of its 64-point tile, then a xor butterfly), FP64 sums over each
+    replicate's tiles, the mean over replicates -- to 1e-12, far below one
+    FP32 rounding of any path."""
+    from fractions import Fraction
+    from exact_rounding import round_exact
+    cs = [(0, 100.0, 1.0, 0, 0), (1, 95.0, 1.0, 0, 0), (0, 105.0, 1.0, 1, 0)]
+    R, P, N, seed = 4, 128, 30, 7
+    opts = nv.make_options(prec=nv.HESTON_FP32, rng=nv.HESTON_RNG_SOBOL_BB, n_shifts=R)
+    gm, gse = nv.results_to_arrays(nv.heston_mc_price_greeks_ex(
+        nv.make_params(**BASE), _gc(nv, cs), R * P, N, seed, opts))
+    rnd = lambda q: round_exact(q, 24)
+    rep_means = np.zeros((R, len(cs), 6))
+    for r in range(R):
+        _, est = nv.heston_qmc_debug_paths(nv.make_params(**BASE), _gc(nv, cs), N, seed, opts, r,
+                                           np.arange(P, dtype=np.uint32))
+        acc = np.zeros((len(cs), 6))
+        for t in range(P // 64):
+            for c in range(len(cs)):
+                for j in range(6):
+                    x = est[t * 64:(t + 1) * 64, c, j]
+                    v = [rnd(Fraction(x[l]) + Fraction(x[l + 32])) for l in range(32)]
+                    for o in (16, 8, 4, 2, 1):
+                        v = [rnd(Fraction(v[l]) + Fraction(v[l ^ o])) for l in range(32)]
+                    acc[c, j] += v[0]
+        rep_means[r] = acc / P
+    mean = rep_means.mean(axis=0)
+    se = rep_means.std(axis=0, ddof=1) / np.sqrt(R)
+    np.testing.assert_allclose(gm, mean, rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(gse, se, rtol=1e-9, atol=1e-14)
