@@ -265,7 +265,10 @@ int heston_mc_reduce_tiles(const double *d_tile_sums, uint64_t n_tiles, uint32_t
  *   - replicate r (of opts->n_shifts) XORs word d%4 of Philox block
  *     (d/4, r, 0, 2) under key rng_seed into dimension d; path index
  *     p = r * P + n with P = n_paths / n_shifts points per replicate.
- *   - u = ((y >> 8) + 1/2) 2^-24, z = Phi^-1(u).
+ *   - u = ((y >> 8) + 1/2) 2^-24, z = Phi^-1(u).  The FP32 kernels evaluate
+ *     Phi^-1 as v P(w), v = 2u - 1, w = -ln(1 - v^2), with polynomials
+ *     fitted for this library: relative error below 3e-7 over all 2^24
+ *     values of u (apart from the lg2 / sqrt approximations, ~2e-8).
  *   - Brownian bridge on the step grid 0..N: node 0 is time N; then
  *     intervals [l, r] with r - l >= 2 are bisected breadth-first at
  *     m = l + (r-l)/2.  Node j drives motion a (Za) with dimension 2j and
