@@ -383,29 +383,32 @@ def test_cached_scratch_reuse_and_release(nv):
         nv.heston_release_cached_memory(64)
 
 
-@pytest.mark.parametrize("prec", ["fp32", "fp64"])
-def test_tile_rows_are_the_sums_of_the_per_path_records(nv, torch_cuda, prec):
+@pytest.mark.parametrize("prec,path_begin,n", [("fp32", 0, 64 * 3 + 19), ("fp64", 0, 64 * 3 + 19),
+                                                ("fp32", (1 << 32) - 128, 256 - 5)])
+def test_tile_rows_are_the_sums_of_the_per_path_records(nv, torch_cuda, prec, path_begin, n):
     """The production path kernel and the per-path record kernel (the one the
     per-path parity tests check against the oracle) compute the same paths:
     each tile row equals, bit for bit, the warp's sums of the per-path
     estimators -- lane l adds paths l and l + 32 of the tile (x0 + x1 and
     fma(x0, x0, x1 * x1), zero past the last path), then a xor butterfly over
-    offsets 16, 8, 4, 2, 1 -- rounded in the path precision."""
+    offsets 16, 8, 4, 2, 1 -- rounded in the path precision.  The third case
+    runs a path range across index 2^32, where the Philox counter's high
+    word (taken per tile in the path kernel) changes."""
     from fractions import Fraction
     torch = torch_cuda
     bits = 24 if prec == "fp32" else 53
     cs = _contracts_for(30)
     nc = len(cs)
-    n, N, seed = 64 * 3 + 19, 30, 5
+    N, seed = 30, 5
     opts = nv.make_options(prec=_prec(nv, prec), stream=torch.cuda.current_stream())
     n_tiles = -(-n // 64)
     rows = torch.zeros(n_tiles * 12 * nc, dtype=torch.float64, device="cuda")
-    nv.heston_mc_launch_tiles(_gp(nv, BASE), _gc(nv, cs), 0, n, N, seed, opts, rows)
+    nv.heston_mc_launch_tiles(_gp(nv, BASE), _gc(nv, cs), path_begin, n, N, seed, opts, rows)
     torch.cuda.synchronize()
     rows = rows.cpu().numpy().reshape(n_tiles, 12 * nc)
     _, est = nv.heston_mc_debug_paths(_gp(nv, BASE), _gc(nv, cs), N, seed,
                                       nv.make_options(prec=_prec(nv, prec)),
-                                      np.arange(n, dtype=np.uint64))
+                                      path_begin + np.arange(n, dtype=np.uint64))
     rnd = lambda q: round_exact(q, bits)
     for t in range(n_tiles):
         for c in range(nc):
