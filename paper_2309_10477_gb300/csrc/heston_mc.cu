@@ -276,6 +276,8 @@ int validate_and_prepare(const heston_params *p, const heston_contract *c, uint3
 }
 
 uint64_t tiles_for(uint64_t n_paths) { return (n_paths + kTile - 1) / kTile; }
+// Threads of a one-contract reduction block: one per (column, part) of the fixed-order sums.
+constexpr int kOneContractSumThreads = 12 * kSumParts;
 uint64_t groups_for(uint64_t n_tiles) { return (n_tiles + kGroupTiles - 1) / kGroupTiles; }
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -360,10 +362,12 @@ cudaError_t launch_reduce(const double *tile_sums, uint64_t n_tiles, int nc, uin
 {
     const int width = 12 * nc;
     const uint64_t ng = groups_for(n_tiles);
-    reduce_groups_kernel<<<(unsigned)ng, 128, 0, st>>>(tile_sums, n_tiles, width, group_sums);
+    // one thread per (column, part) pair of the fixed-order sums: 8 x 12 per contract
+    const int threads = std::min(1024, ((8 * width + 31) / 32) * 32);
+    reduce_groups_kernel<<<(unsigned)ng, threads, 0, st>>>(tile_sums, n_tiles, width, group_sums);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    reduce_final_kernel<<<1, 128, 0, st>>>(group_sums, ng, nc, (double)n_paths, gamma_nan ? 1 : 0, out);
+    reduce_final_kernel<<<1, threads, 0, st>>>(group_sums, ng, nc, (double)n_paths, gamma_nan ? 1 : 0, out);
     return cudaGetLastError();
 }
 
@@ -905,10 +909,10 @@ int batch_launch(const heston_batch_plan *plan, const void *d_desc, const heston
     const cudaError_t e = plan->trunc == HESTON_TRUNC_FULL ? launch_batch_t<0>(a, o, st) : launch_batch_t<1>(a, o, st);
     if (e != cudaSuccess) return HESTON_ERR_CUDA;
     double *groups = (double *)(w + W.off_groups);
-    batch_reduce_groups_kernel<<<(unsigned)plan->total_groups, 64, 0, st>>>(a.items, a.group_begin, n,
+    batch_reduce_groups_kernel<<<(unsigned)plan->total_groups, kOneContractSumThreads, 0, st>>>(a.items, a.group_begin, n,
                                                                             a.rows, groups);
     if (cudaGetLastError() != cudaSuccess) return HESTON_ERR_CUDA;
-    batch_reduce_final_kernel<<<n, 64, 0, st>>>(a.items, groups, d_out);
+    batch_reduce_final_kernel<<<n, kOneContractSumThreads, 0, st>>>(a.items, groups, d_out);
     return cudaGetLastError() == cudaSuccess ? HESTON_OK : HESTON_ERR_CUDA;
 }
 
@@ -1268,10 +1272,10 @@ void srv_loop(heston_server *s)
             // after the previous round's tiles (other stream) too
             if (nf) {
                 cudaStreamWaitEvent(st, s->ev_kern[1 - b], 0);
-                server_reduce_groups_kernel<<<(unsigned)gacc, 64, 0, st>>>(
+                server_reduce_groups_kernel<<<(unsigned)gacc, kOneContractSumThreads, 0, st>>>(
                     s->d_slots, (const uint32_t *)(dp + L.fs), (const uint64_t *)(dp + L.fg), nf, s->d_pool,
                     s->d_groups[b]);
-                server_reduce_final_kernel<<<nf, 64, 0, st>>>(s->d_slots, (const uint32_t *)(dp + L.fs),
+                server_reduce_final_kernel<<<nf, kOneContractSumThreads, 0, st>>>(s->d_slots, (const uint32_t *)(dp + L.fs),
                                                               (const uint64_t *)(dp + L.fg), s->d_groups[b],
                                                               s->d_res[b]);
                 cudaMemcpyAsync(s->h_res[b], s->d_res[b], (size_t)nf * 12u * sizeof(double),
