@@ -158,3 +158,29 @@ def test_unstable_tangents_are_flagged(nv):
     finite = all(np.isfinite([r.vega, r.theta, r.se[3], r.se[5]]))
     assert (rc == nv.HESTON_WARN_TANGENT_UNSTABLE) == (not finite)
     assert np.isfinite([r.price, r.delta, r.gamma, r.rho]).all()
+
+
+def test_full_batched_mix_sampled_against_the_oracle(nv):
+    """The 1024-contract seeded mix of the batched benchmark (K~U[70,130],
+    T in {0.25,0.5,1,2}, paths 2^14..2^20, steps 50..500, European/Asian),
+    priced in one persistent launch with the benchmark's per-contract seeds.
+    The four contracts with the least work are recomputed at full size by
+    the FP64 oracle: every estimate within 3 SE, and price, Delta, Gamma and
+    Rho (Vega/Theta too where Feller holds) within 1e-4 of the oracle."""
+    w = wl.multi_strike_fp32()
+    mix = wl.batched_contracts(1024)
+    items = [nv.make_batch_item(nv.make_params(**d["params"]), nv.make_contract(*d["contract"]),
+                                d["n_paths"], d["n_steps"], w.seed + 1000003 * i)
+             for i, d in enumerate(mix)]
+    got = _arr(nv.heston_mc_price_greeks_batch(items, nv.make_options(prec=nv.HESTON_FP32)), nv)
+    work = [d["n_paths"] * d["n_steps"] for d in mix]
+    for i in np.argsort(work)[:4]:
+        it, d = items[i], mix[i]
+        P = oracle.Params(**d["params"])
+        om, ose = oracle.mc_price_greeks(P, [oracle.Contract(*d["contract"])], it.n_paths,
+                                         it.n_steps, it.rng_seed)
+        diff = np.abs(got[i, :6] - om[0])
+        assert (diff <= 3 * ose[0] + 1e-9).all(), (i, diff, ose[0])
+        p = d["params"]
+        check = [0, 1, 2, 4] + ([3, 5] if 2 * p["kappa"] * p["theta"] >= p["xi"] ** 2 else [])
+        assert (diff[check] <= 1e-4 * np.maximum(1.0, np.abs(om[0][check]))).all(), (i, diff, om[0])
