@@ -658,7 +658,7 @@ def run_gpu(args):
             line["serving_variant"] = serving
         if schemes is not None:
             line["scheme_variants"] = schemes
-        if not args.no_cpu_baseline:
+        if not args.no_cpu_baseline and world == 1:      # the oracle baseline: rank 0 at N = 1 only
             line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
         print(json.dumps(line), flush=True)
     if world > 1:
