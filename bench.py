@@ -635,7 +635,7 @@ def run_gpu(args):
                     "h2d_bytes_per_step": ctypes.sizeof(nv.heston_params)
                     + nc * ctypes.sizeof(nv.heston_contract),
                     "d2h_bytes_per_step": nc * 12 * 8},
-            "gpu_launches": 3 * args.steps,
+            "gpu_launches": 3 * args.steps * world,         # path kernel + 2 reductions per step, all ranks
             "roofline": {"bound": "alu", "kernel": "heston_paths_kernel<float,FULL,ASIAN>",
                          "achieved": achieved_tinst, "peak": peak_tinst,
                          "unit": f"T issue slots/s ({ALGO_SLOTS_PER_PATH_STEP} algorithmic slots per "
