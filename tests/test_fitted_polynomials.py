@@ -46,13 +46,13 @@ def test_box_muller_radius_polynomial():
 def _qmc_coefficients(src):
     body = src[src.index("__device__ __forceinline__ float qmc_normal(uint32_t y)"):]
     body = body[:body.index("\n}\n")]
-    central = body[body.index("const float t = w - 3.125f;"):body.index("const float t = sqrt_approx(w) - 3.0f;")]
-    tail = body[body.index("const float t = sqrt_approx(w) - 3.0f;"):]
+    central = body[body.index("const float t = add_(w, -3.125f);"):body.index("const float t = add_(sqrt_approx(w), -3.0f);")]
+    tail = body[body.index("const float t = add_(sqrt_approx(w), -3.0f);"):]
     num = r"(-?[0-9.]+(?:e-?[0-9]+)?)f"
 
     def horner_coefs(part):
-        first = re.search(rf"fmaf\(t, {num}, {num}\)", part)
-        rest = re.findall(rf"fmaf\(t, p2?, {num}\)", part)
+        first = re.search(rf"fma_\(t, {num}, {num}\)", part)
+        rest = re.findall(rf"fma_\(t, p2?, {num}\)", part)
         return [float(first.group(1)), float(first.group(2))] + [float(v) for v in rest]
 
     return horner_coefs(central), horner_coefs(tail)
