@@ -17,9 +17,10 @@
 //
 // GPU design: one lane carries two paths through all N steps in registers
 // (Philox4x32-10 -> Box-Muller -> correlate -> Milstein step -> tangents ->
-// Asian sums); a warp owns 64-path tiles and reduces each tile's estimators
-// with shuffles; tile rows go to a workspace and two fixed-order kernels
-// reduce them in FP64.  No per-path or per-step data touches memory.
+// Asian sums), in FP32 as f32x2 instructions on the pair; a warp owns 64-path
+// tiles and reduces each tile's estimators with shuffles; tile rows go to a
+// workspace and two fixed-order kernels reduce them in FP64.  No per-path or
+// per-step data touches memory.
 #include <cuda_runtime.h>
 
 #include <cmath>
