@@ -32,8 +32,11 @@ def _run(nv, torch, params, c, n, N, seed):
     return out.cpu().numpy(), g.cpu().numpy()
 
 
+# N = 300 and 1024 take the backward kernel's 32-step segment arrays (C = 18, 32);
+# the others the 16-step ones
 @pytest.mark.parametrize("payoff,put,M,N,n", [(0, 0, 0, 64, 1 << 15), (1, 0, 0, 252, 1 << 14),
-                                              (1, 1, 4, 32, (1 << 15) + 37), (0, 1, 0, 7, 5000)])
+                                              (1, 1, 4, 32, (1 << 15) + 37), (0, 1, 0, 7, 5000),
+                                              (1, 0, 0, 300, 4096 + 5), (0, 0, 0, 1024, 2048)])
 def test_adjoint_matches_oracle_forward_mode(nv, payoff, put, M, N, n):
     import torch
     c = nv.make_contract(payoff, 100.0, 1.0, put, M)
@@ -84,6 +87,7 @@ def test_adjoint_rejections(nv):
         with pytest.raises(nv.HestonError) as e:
             nv.heston_mc_adjoint_forward(p, c, 1024, 10, 1, opts, ws, 8 << 20, out)
         assert e.value.status == nv.HESTON_ERR_UNSUPPORTED
-    with pytest.raises(nv.HestonError) as e:
-        nv.heston_adjoint_workspace_bytes(1024, 2000)
-    assert e.value.status == nv.HESTON_ERR_UNSUPPORTED
+    for N in (1025, 2000):                       # segments of more than 32 steps
+        with pytest.raises(nv.HestonError) as e:
+            nv.heston_adjoint_workspace_bytes(1024, N)
+        assert e.value.status == nv.HESTON_ERR_UNSUPPORTED
