@@ -155,3 +155,19 @@ def test_qmc_estimates_are_the_sums_of_the_per_path_records(nv):
     se = rep_means.std(axis=0, ddof=1) / np.sqrt(R)
     np.testing.assert_allclose(gm, mean, rtol=1e-12, atol=1e-14)
     np.testing.assert_allclose(gse, se, rtol=1e-9, atol=1e-14)
+
+
+def test_qmc_launch_shape_does_not_change_bits(nv):
+    """The QMC kernel stages one row of Sobol words per warp in shared memory,
+    sized by the block: other grid and block shapes give the same bits."""
+    cs = [(0, 100.0, 1.0, 0, 0), (1, 95.0, 1.0, 0, 0), (1, 105.0, 1.0, 1, 0)]
+    R, P, N = 4, 1024, 61
+    ref = None
+    for grid, block in ((0, 0), (3, 64), (0, 32), (700, 128)):
+        opts = nv.make_options(prec=nv.HESTON_FP32, rng=nv.HESTON_RNG_SOBOL_BB, n_shifts=R,
+                               grid_ctas=grid, block_threads=block)
+        got = np.concatenate(nv.results_to_arrays(nv.heston_mc_price_greeks_ex(
+            nv.make_params(**BASE), _gc(nv, cs), R * P, N, 3, opts)), axis=1)
+        if ref is None:
+            ref = got
+        assert np.array_equal(got, ref), (grid, block)
