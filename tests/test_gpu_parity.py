@@ -422,3 +422,21 @@ def test_tile_rows_are_the_sums_of_the_per_path_records(nv, torch_cuda, prec, pa
                     sxx = [rnd(Fraction(sxx[l]) + Fraction(sxx[l ^ o])) for l in range(32)]
                 assert rows[t, c * 6 + j] == sx[0], (t, c, j)
                 assert rows[t, 6 * nc + c * 6 + j] == sxx[0], (t, c, j)
+
+
+def test_eight_contracts_the_widest_tile_row(nv):
+    """HESTON_MAX_CONTRACTS = 8 on one set of paths: tile rows of 96 columns,
+    the widest the epilogue and the fixed-order reductions handle; FP64 to
+    1e-9 of the oracle (contracts on one set of paths share T and the Asian
+    dates).  Nine contracts are rejected."""
+    cs = [(0, 90.0, 1.0, 0, 0), (0, 100.0, 1.0, 1, 0), (1, 95.0, 1.0, 0, 0), (1, 105.0, 1.0, 1, 0),
+          (0, 110.0, 1.0, 0, 0), (1, 100.0, 1.0, 0, 0), (0, 80.0, 1.0, 1, 0), (1, 120.0, 1.0, 0, 0)]
+    assert len(cs) == nv.HESTON_MAX_CONTRACTS
+    n, N = 64 * 40 + 3, 24
+    gm, gse = _gpu_estimates(nv, BASE, cs, n, N, 77, nv.HESTON_FP64)
+    om, ose = oracle.mc_price_greeks(oracle.Params(**BASE), _oc(cs), n, N, 77)
+    np.testing.assert_allclose(gm, om, rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(gse, ose, rtol=1e-9, atol=1e-12)
+    with pytest.raises(nv.HestonError) as e:
+        _gpu_estimates(nv, BASE, cs + [cs[0]], n, N, 77, nv.HESTON_FP64)
+    assert e.value.status == nv.HESTON_ERR_INVALID_ARG
