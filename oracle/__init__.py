@@ -45,13 +45,13 @@ EUROPEAN, ASIAN = 0, 1
 
 
 def build(force: bool = False) -> str:
-    """Compile heston_oracle.c with gcc (-O2, no fast-math, OpenMP)."""
+    """Compile heston_oracle.c with gcc (-O3, no fast-math, no FMA contraction, OpenMP)."""
     with _lock:
         if (not force and os.path.exists(_LIB)
                 and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
             return _LIB
         tmp = _LIB + f".tmp{os.getpid()}"
-        base = ["gcc", "-std=c11", "-O2", "-fno-fast-math", "-ffp-contract=off",
+        base = ["gcc", "-std=c11", "-O3", "-fno-fast-math", "-ffp-contract=off",
                 "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
         try:
             subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True,
@@ -84,6 +84,9 @@ def _load():
         lib.orc_mc_sums.argtypes = [P(_Params), P(_Contract), u32, u64, u64, u32, u64, i32, i32,
                                     i32, P(d), P(d)]
         lib.orc_mc_sums.restype = i32
+        lib.orc_mc_sums_perturbed.argtypes = [P(_Params), P(_Contract), u32, u64, u64, u32, u64, i32,
+                                              i32, i32, d, d, u64, P(d), P(d)]
+        lib.orc_mc_sums_perturbed.restype = i32
         lib.orc_debug_paths.argtypes = [P(_Params), P(_Contract), u32, P(u64), u64, u32, u64, i32,
                                         i32, P(d), P(d)]
         lib.orc_debug_paths.restype = i32
@@ -97,7 +100,11 @@ def _load():
         lib.orc_mc_gradient.restype = i32
         lib.orc_debug_gradients.argtypes = [P(_Params), P(_Contract), P(u64), u64, u32, u64, P(d)]
         lib.orc_debug_gradients.restype = i32
+        lib.orc_gradients_from_normals.argtypes = [P(_Params), P(_Contract), u32, u64, P(d), P(d), P(d)]
+        lib.orc_gradients_from_normals.restype = i32
         lib.orc_max_threads.restype = i32
+        lib.orc_set_threads.argtypes = [i32]
+        lib.orc_set_threads.restype = None
         _lib = lib
     return _lib
 
@@ -187,6 +194,24 @@ def mc_sums(params: Params, contracts, n_paths, n_steps, seed, trunc=TRUNC_FULL,
                          trunc, scheme, n_threads, _dptr(s), _dptr(s2))
     _check_rc(rc)
     return s.reshape(-1, 6), s2.reshape(-1, 6)
+
+
+def mc_price_greeks_perturbed(params: Params, contracts, n_paths, n_steps, seed, eps_abs, eps_rel,
+                              pert_seed, trunc=TRUNC_FULL, scheme=SCHEME_MILSTEIN, n_threads=0):
+    """mc_price_greeks with every normal moved by (eps_abs + eps_rel R) (2U - 1),
+    R = sqrt(Za^2 + Zb^2), U from a separate Philox stream keyed by pert_seed:
+    a probe of how far the estimates move under perturbations of that size."""
+    lib = _load()
+    cs = _contracts(contracts)
+    E = 6 * len(contracts)
+    s = np.zeros(E)
+    s2 = np.zeros(E)
+    p = params._c()
+    rc = lib.orc_mc_sums_perturbed(ctypes.byref(p), cs, len(contracts), 0, n_paths, n_steps, seed,
+                                   trunc, scheme, n_threads, eps_abs, eps_rel, pert_seed, _dptr(s),
+                                   _dptr(s2))
+    _check_rc(rc)
+    return mean_se(s.reshape(-1, 6), s2.reshape(-1, 6), n_paths)
 
 
 def mean_se(s, s2, n):
@@ -280,5 +305,23 @@ def debug_gradients(params: Params, contract: Contract, paths, n_steps, seed):
     return out
 
 
+def gradients_from_normals(params: Params, contract: Contract, za, zb):
+    """Per-path (payoff, 7 derivatives) from given normals (n_paths, N): (n, 8)."""
+    lib = _load()
+    za = np.ascontiguousarray(za, dtype=np.float64)
+    zb = np.ascontiguousarray(zb, dtype=np.float64)
+    n, N = za.shape
+    out = np.zeros((n, 8))
+    p = params._c()
+    _check_rc(lib.orc_gradients_from_normals(ctypes.byref(p), _contracts([contract]), N, n, _dptr(za),
+                                             _dptr(zb), _dptr(out)))
+    return out
+
+
 def max_threads() -> int:
     return int(_load().orc_max_threads())
+
+
+def set_threads(n: int) -> None:
+    """Threads of later calls that take no count of their own (0: one per core)."""
+    _load().orc_set_threads(int(n))

@@ -471,9 +471,57 @@ void orc_estimators(const orc_params *p, const orc_contract *c, uint32_t N,
  * sumsq[c*6+e] = sum_x^2 over the paths.  All contracts must share T (they
  * share the paths) and all Asian contracts must share M.
  * Returns 0, or -1 on invalid input. */
+/* Sensitivity probe support: move each normal of step k of a path by
+ * (eps_abs + eps_rel R) (2U - 1), R = sqrt(Za^2 + Zb^2), with U uniform on
+ * [0, 1) from Philox4x32-10 (key pert_seed, counter (k / 2, path_lo,
+ * path_hi, 7); words 0-1 for even k, 2-3 for odd k; U = (w >> 8) 2^-24). */
+static void orc_perturb_normals(uint64_t pert_seed, uint64_t path, uint32_t N, double eps_abs,
+                                double eps_rel, double *Za, double *Zb)
+{
+    const uint32_t key[2] = { (uint32_t)pert_seed, (uint32_t)(pert_seed >> 32) };
+    uint32_t x[4] = { 0, 0, 0, 0 };
+    for (uint32_t k = 0; k < N; ++k) {
+        if ((k & 1u) == 0) {
+            const uint32_t ctr[4] = { k / 2u, (uint32_t)path, (uint32_t)(path >> 32), 7u };
+            orc_philox4x32_10(ctr, key, x);
+        }
+        const uint32_t wa = (k & 1u) ? x[2] : x[0], wb = (k & 1u) ? x[3] : x[1];
+        const double bound = eps_abs + eps_rel * sqrt(Za[k] * Za[k] + Zb[k] * Zb[k]);
+        Za[k] += bound * (2.0 * ldexp((double)(wa >> 8), -24) - 1.0);
+        Zb[k] += bound * (2.0 * ldexp((double)(wb >> 8), -24) - 1.0);
+    }
+}
+
+static int orc_mc_sums_impl(const orc_params *p, const orc_contract *contracts, uint32_t n_contracts,
+                            uint64_t path_begin, uint64_t n_paths, uint32_t N, uint64_t seed, int trunc,
+                            int scheme, int n_threads, double eps_abs, double eps_rel,
+                            uint64_t pert_seed, double *sum, double *sumsq);
+
 int orc_mc_sums(const orc_params *p, const orc_contract *contracts, uint32_t n_contracts,
                 uint64_t path_begin, uint64_t n_paths, uint32_t N, uint64_t seed, int trunc,
                 int scheme, int n_threads, double *sum, double *sumsq)
+{
+    return orc_mc_sums_impl(p, contracts, n_contracts, path_begin, n_paths, N, seed, trunc, scheme,
+                            n_threads, 0.0, 0.0, 0u, sum, sumsq);
+}
+
+/* orc_mc_sums with every normal perturbed as in orc_perturb_normals: how far
+ * the estimates move under perturbations of a given size (the conditioning
+ * of an estimate for a path computed at lower precision).  Test support. */
+int orc_mc_sums_perturbed(const orc_params *p, const orc_contract *contracts, uint32_t n_contracts,
+                          uint64_t path_begin, uint64_t n_paths, uint32_t N, uint64_t seed, int trunc,
+                          int scheme, int n_threads, double eps_abs, double eps_rel,
+                          uint64_t pert_seed, double *sum, double *sumsq)
+{
+    if (!(eps_abs >= 0.0) || !(eps_rel >= 0.0)) return -1;
+    return orc_mc_sums_impl(p, contracts, n_contracts, path_begin, n_paths, N, seed, trunc, scheme,
+                            n_threads, eps_abs, eps_rel, pert_seed, sum, sumsq);
+}
+
+static int orc_mc_sums_impl(const orc_params *p, const orc_contract *contracts, uint32_t n_contracts,
+                            uint64_t path_begin, uint64_t n_paths, uint32_t N, uint64_t seed, int trunc,
+                            int scheme, int n_threads, double eps_abs, double eps_rel,
+                            uint64_t pert_seed, double *sum, double *sumsq)
 {
     if (n_contracts == 0 || N == 0 || !orc_scheme_ok(p, trunc, scheme)) return -1;
     const double T = contracts[0].T;
@@ -492,6 +540,7 @@ int orc_mc_sums(const orc_params *p, const orc_contract *contracts, uint32_t n_c
     if (!csum) return -1;
 
 #ifdef _OPENMP
+    const int threads_before = omp_get_max_threads();
     if (n_threads > 0) omp_set_num_threads(n_threads);
 #pragma omp parallel
 #endif
@@ -509,6 +558,8 @@ int orc_mc_sums(const orc_params *p, const orc_contract *contracts, uint32_t n_c
             uint64_t hi = lo + ORC_CHUNK < n_paths ? lo + ORC_CHUNK : n_paths;
             for (uint64_t i = lo; i < hi; ++i) {
                 orc_path_normals(seed, path_begin + i, N, 0u, Za, Zb);
+                if (eps_abs > 0.0 || eps_rel > 0.0)
+                    orc_perturb_normals(pert_seed, path_begin + i, N, eps_abs, eps_rel, Za, Zb);
                 orc_scheme_path(p, T, N, M, trunc, scheme, Za, Zb, &w, NULL, NULL);
                 for (uint32_t c = 0; c < n_contracts; ++c) {
                     orc_estimators(p, &contracts[c], N, &w, est);
@@ -523,6 +574,9 @@ int orc_mc_sums(const orc_params *p, const orc_contract *contracts, uint32_t n_c
         free(Zb);
     }
 
+#ifdef _OPENMP
+    omp_set_num_threads(threads_before);      /* n_threads applies to this call only */
+#endif
     for (uint32_t e = 0; e < E; ++e) { sum[e] = 0.0; sumsq[e] = 0.0; }
     for (uint64_t ch = 0; ch < n_chunks; ++ch) {
         const double *s = csum + (size_t)ch * E * 2;
@@ -724,6 +778,23 @@ int orc_mc_gradient(const orc_params *p, const orc_contract *c, uint64_t n_paths
     return 0;
 }
 
+/* Per-path gradients from given normals (n_paths x N each, row-major),
+ * test support: out[i*8 ...] = (payoff, 7 derivatives). */
+int orc_gradients_from_normals(const orc_params *p, const orc_contract *c, uint32_t N,
+                               uint64_t n_paths, const double *Za, const double *Zb, double *out)
+{
+    if (N == 0) return -1;
+    const uint32_t M = c->n_monitor ? c->n_monitor : N;
+    if (N % M) return -1;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+    for (int64_t i = 0; i < (int64_t)n_paths; ++i)
+        orc_path_gradient(p, c, N, Za + (size_t)i * N, Zb + (size_t)i * N, out + (size_t)i * 8,
+                          out + (size_t)i * 8 + 1);
+    return 0;
+}
+
 /* Per-path gradients for a list of paths (test support): out[i*8 ...] =
  * (payoff, 7 derivatives). */
 int orc_debug_gradients(const orc_params *p, const orc_contract *c, const uint64_t *paths,
@@ -737,6 +808,17 @@ int orc_debug_gradients(const orc_params *p, const orc_contract *c, const uint64
     free(Za);
     free(Zb);
     return 0;
+}
+
+/* Threads of every later parallel call that does not set its own count
+ * (n <= 0: one per core); the benchmark's one-core timings use it. */
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    omp_set_num_threads(n > 0 ? n : omp_get_num_procs());
+#else
+    (void)n;
+#endif
 }
 
 int orc_max_threads(void)
