@@ -5,8 +5,8 @@ contiguous, 64-path-aligned range with ``heston_mc_launch_tiles``; the
 per-tile partial-sum rows of all ranks, concatenated in rank order, are
 exactly the rows of the unsharded run, so ``heston_mc_reduce_tiles`` over
 them gives bit-identical estimates on every rank.  The only exchange is one
-gather of those rows (a few hundred bytes per tile-group), done here with
-``torch.distributed``.
+gather of those rows (12 doubles per contract and 64-path tile), done here
+with ``torch.distributed``.
 """
 from __future__ import annotations
 
@@ -46,23 +46,44 @@ def gather_tile_rows(local_rows: torch.Tensor, n_paths: int, world: int, group=N
     return torch.cat([bufs[r][: counts[r]] for r in range(world)], dim=0)
 
 
-def price_greeks_sharded(params, contracts, n_paths, n_steps, rng_seed, options, group=None):
+def _launch_tiles_native(params, contracts, path_begin, n, n_steps, rng_seed, options, rows):
+    native.heston_mc_launch_tiles(params, contracts, path_begin, n, n_steps, rng_seed, options, rows)
+
+
+def _reduce_tiles_native(rows, n_tiles, n_contracts, n_paths, device):
+    ws_bytes = native.heston_mc_workspace_bytes(n_contracts, n_paths)
+    ws = torch.empty(ws_bytes // 8 + 1, dtype=torch.float64, device=device)
+    out = torch.empty(n_contracts * 12, dtype=torch.float64, device=device)
+    native.heston_mc_reduce_tiles(rows, n_tiles, n_contracts, n_paths, ws, ws_bytes, out,
+                                  torch.cuda.current_stream())
+    return out
+
+
+def price_greeks_sharded(params, contracts, n_paths, n_steps, rng_seed, options, group=None,
+                         device=None, launch_tiles=None, reduce_tiles=None):
     """Estimate on this rank's path range, gather the tile rows, reduce them
-    in the fixed order: every rank returns the single-GPU result (C, 12)."""
+    in the fixed order: every rank returns the single-GPU result (C, 12) as a
+    host tensor (per contract: 6 estimates, then their 6 standard errors).
+
+    device: where the rows live (default: the current CUDA device).
+    launch_tiles(params, contracts, path_begin, n, n_steps, seed, options, rows)
+    and reduce_tiles(rows, n_tiles, n_contracts, n_paths, device) -> (12 C,)
+    default to the library's heston_mc_launch_tiles / heston_mc_reduce_tiles;
+    host-only tests replace them."""
     world = dist.get_world_size(group) if dist.is_initialized() else 1
     rank = dist.get_rank(group) if dist.is_initialized() else 0
+    if device is None:
+        device = torch.device("cuda", torch.cuda.current_device())
+    launch_tiles = launch_tiles or _launch_tiles_native
+    reduce_tiles = reduce_tiles or _reduce_tiles_native
     b, e = shard_bounds(n_paths, world, rank)
     nc = len(contracts)
-    dev = torch.device("cuda", torch.cuda.current_device())
-    local = torch.zeros((max(1, -(-(e - b) // TILE)), 12 * nc), dtype=torch.float64, device=dev)
+    local_tiles = -(-(e - b) // TILE)
+    local = torch.zeros((max(1, local_tiles), 12 * nc), dtype=torch.float64, device=device)
     if e > b:
-        native.heston_mc_launch_tiles(params, contracts, b, e - b, n_steps, rng_seed, options, local)
-    rows = gather_tile_rows(local[: -(-(e - b) // TILE)], n_paths, world, group) if world > 1 else local
-    n_tiles = rows.shape[0]
-    ws_bytes = native.heston_mc_workspace_bytes(nc, n_paths)
-    ws = torch.empty(ws_bytes // 8 + 1, dtype=torch.float64, device=dev)
-    out = torch.empty(nc * 12, dtype=torch.float64, device=dev)
-    native.heston_mc_reduce_tiles(rows.contiguous(), n_tiles, nc, n_paths, ws, ws_bytes, out,
-                                  torch.cuda.current_stream())
-    torch.cuda.current_stream().synchronize()
+        launch_tiles(params, contracts, b, e - b, n_steps, rng_seed, options, local)
+    rows = gather_tile_rows(local[:local_tiles], n_paths, world, group) if world > 1 else local[:local_tiles]
+    out = reduce_tiles(rows.contiguous(), rows.shape[0], nc, n_paths, device)
+    if out.is_cuda:
+        torch.cuda.current_stream().synchronize()
     return out.view(nc, 12).cpu()

@@ -81,3 +81,60 @@ def test_shard_bounds_cover_exactly_and_align():
             assert all(b % 64 == 0 for b, e in spans if e > b)
             sizes = [-(-(e - b) // 64) for b, e in spans]
             assert max(sizes) - min(sizes) <= 1
+
+
+# ---------------------------------------------------------------------------
+# price_greeks_sharded end to end on gloo ranks: the oracle's tile rows stand
+# in for heston_mc_launch_tiles and a fixed-order host sum for
+# heston_mc_reduce_tiles; every rank must return the single-process result.
+# ---------------------------------------------------------------------------
+
+def _launch_stub(params, contracts, path_begin, n, n_steps, seed, options, rows):
+    rows[:] = torch.from_numpy(_tile_rows(path_begin, path_begin + n))
+
+
+def _reduce_stub(rows, n_tiles, n_contracts, n_paths, device):
+    assert rows.shape == (n_tiles, 12 * n_contracts)
+    tot = np.zeros(12 * n_contracts)
+    for t in range(n_tiles):                 # fixed order: tile rows in path order
+        tot += rows[t].numpy()
+    E = 6 * n_contracts
+    mean = tot[:E] / n_paths
+    se = np.sqrt(np.maximum((tot[E:] - n_paths * mean * mean) / (n_paths - 1), 0.0) / n_paths)
+    return torch.from_numpy(np.concatenate([mean.reshape(-1, 6), se.reshape(-1, 6)], axis=1).ravel())
+
+
+def _sharded_worker(rank, world, port, n_paths, q):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        out = parallel.price_greeks_sharded(None, CS, n_paths, N_STEPS, SEED, None,
+                                            device=torch.device("cpu"), launch_tiles=_launch_stub,
+                                            reduce_tiles=_reduce_stub)
+        q.put((rank, out.numpy()))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world,n_paths", [(2, 64 * 7 + 9), (3, 64 * 3)])
+def test_gloo_price_greeks_sharded_equals_one_process(world, n_paths):
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_sharded_worker, args=(r, world, port, n_paths, q))
+             for r in range(world)]
+    for p in procs:
+        p.start()
+    got = dict(q.get(timeout=120) for _ in range(world))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    alone = parallel.price_greeks_sharded(None, CS, n_paths, N_STEPS, SEED, None,
+                                          device=torch.device("cpu"), launch_tiles=_launch_stub,
+                                          reduce_tiles=_reduce_stub).numpy()
+    for r in range(world):
+        assert np.array_equal(got[r], alone), r
+    om, ose = oracle.mc_price_greeks(P, CS, n_paths, N_STEPS, SEED)
+    np.testing.assert_allclose(alone[:, :6], om, rtol=1e-12, atol=1e-13)
+    np.testing.assert_allclose(alone[:, 6:], ose, rtol=1e-9, atol=1e-13)
