@@ -47,7 +47,19 @@ UNIT = "path-steps/s"
 # per path-step against 1 slot per lane per clock.
 ALGO_OPS_PER_PATH_STEP = 88
 ALGO_SLOTS_PER_PATH_STEP = 64
+# The same work counted one issue slot per operation with Philox at ~45
+# integer operations and no packing: 92 slots per path-step.
+SCALAR_SLOTS_PER_PATH_STEP = 92
 ISSUE_LANES_PER_SM_CLK = 128          # 4 SM sub-partitions x 1 warp-instruction x 32 lanes
+# FP64 path (one European call): the explicit FP64 arithmetic per path-step,
+# counted from the operations the method needs -- the Milstein step with its
+# tangents and Gamma weights 38 (the correlation 4, V+ dt and u 2, du/dv0 and
+# du/dT 6, Gamma weights 2, ln S and its tangents 8, V and its tangents 13,
+# the Milstein term 3) and Box-Muller 9 (two int->double conversions, five
+# scalings and products, two final products) -- 47, plus five FP64 special
+# functions (log, sqrt, sin and cos of 2 pi u2, 1 / sqrt(V dt)) that run on
+# the same pipe and are not counted.
+FP64_OPS_PER_PATH_STEP = 47
 FLUSH_BYTES = 256 << 20               # > 129 MB L2
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "heston_paths_kernel_multi_strike_2p22.md")
 KERNEL_SOURCE = os.path.join(ROOT, "paper_2309_10477_gb300", "csrc", "heston_device.cuh")
@@ -103,6 +115,17 @@ class ClockSampler:
                 self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
+
+    def summary_between(self, t0, t1):
+        """Median SM clock of the samples taken between host times t0 and t1."""
+        sm = []
+        for t, r in self.rows:
+            if t0 <= t <= t1:
+                try:
+                    sm.append(float(r[1]))
+                except (ValueError, IndexError):
+                    pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "samples": len(sm)}
 
     def summary(self):
         windows = []
@@ -176,6 +199,104 @@ def _time_oracle(w, P, cs, n_sample, reps=1):
         dt = time.perf_counter() - t0
         best = dt if best is None else min(best, dt)
     return n_sample * w.n_steps / best, best
+
+
+def host_info():
+    """nproc, the CPU model and its maximum clock, from os and lscpu."""
+    info = {"nproc": os.cpu_count()}
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            k, _, v = line.partition(":")
+            k, v = k.strip(), v.strip()
+            if k == "Model name":
+                info["model"] = v
+            elif k == "CPU max MHz":
+                info["max_mhz"] = float(v)
+            elif k == "Architecture":
+                info["arch"] = v
+    except (OSError, subprocess.SubprocessError, ValueError):
+        pass
+    return info
+
+
+def _timed(fn):
+    t0 = time.perf_counter()
+    fn()
+    return time.perf_counter() - t0
+
+
+def cpu_baselines(budget_s: float = 3.0):
+    """The oracle, as it stands, beside each configuration, on all host cores
+    and on one: path-steps/s and Greek-sets/s (the oracle's SE at the same
+    path count is the SE target, so these are rates at the same SE).  Each
+    sample is sized to about budget_s seconds."""
+    import oracle
+    from paper_2309_10477_gb300 import workloads as wl
+    all_threads = oracle.max_threads()
+    out = {"host": host_info(), "threads_all": all_threads}
+
+    def rate(run, n_full, path_steps_per_path, label, greek_sets):
+        res = {}
+        for mode, threads in (("all_cores", all_threads), ("one_core", 1)):
+            oracle.set_threads(threads)
+            try:
+                n = 4096 * threads
+                dt = _timed(lambda: run(n))
+                n = int(min(n_full, max(4096, n * budget_s / max(dt, 1e-6))) // 4096 * 4096) or 4096
+                dt = _timed(lambda: run(n))
+            finally:
+                oracle.set_threads(0)
+            ps = n * path_steps_per_path / dt
+            res[mode] = {"path_steps_per_s": ps, "cores": threads,
+                         "greek_sets_per_s": greek_sets * ps / (n_full * path_steps_per_path),
+                         "sample": f"{n} of {n_full} paths ({dt:.1f} s)"}
+        res["workload"] = label
+        return res
+
+    # config 1: one European call, 2^16 x 100, FP64
+    w1 = wl.single_european_fp64()
+    P1, C1 = oracle.Params(**w1.params), [oracle.Contract(*c) for c in w1.contracts]
+    out["single_european_fp64"] = rate(lambda n: oracle.mc_sums(P1, C1, n, w1.n_steps, w1.seed),
+                                       w1.n_paths, w1.n_steps, w1.name, 1)
+    # config 2: the headline workload
+    w2 = wl.multi_strike_fp32()
+    P2, C2 = oracle.Params(**w2.params), [oracle.Contract(*c) for c in w2.contracts]
+    out["multi_strike"] = rate(lambda n: oracle.mc_sums(P2, C2, n, w2.n_steps, w2.seed),
+                               w2.n_paths, w2.n_steps, w2.name, len(C2))
+    # config 3: a 64-contract subset of the batched mix (every 16th contract), each
+    # contract's paths capped to the sample, scaled by path-steps to the whole mix
+    mix = wl.batched_contracts(1024)
+    sub = mix[::16]
+    total_ps = sum(d["n_paths"] * d["n_steps"] for d in mix)
+
+    def run_mix(cap):
+        for d in sub:
+            oracle.mc_sums(oracle.Params(**d["params"]), [oracle.Contract(*d["contract"])],
+                           min(cap, d["n_paths"]), d["n_steps"], 42)
+    res3 = {}
+    for mode, threads in (("all_cores", all_threads), ("one_core", 1)):
+        # each contract's paths are capped at one 4096-path chunk per thread, so that
+        # every thread has work on the contracts large enough to need it
+        cap = 4096 * threads
+        oracle.set_threads(threads)
+        try:
+            dt = _timed(lambda: run_mix(cap))
+        finally:
+            oracle.set_threads(0)
+        ps = sum(min(cap, d["n_paths"]) * d["n_steps"] for d in sub) / dt
+        res3[mode] = {"path_steps_per_s": ps, "cores": threads,
+                      "greek_sets_per_s": 1024 * ps / total_ps,
+                      "sample": f"64 of the 1024 contracts (every 16th), up to {cap} paths each "
+                                f"({dt:.1f} s), scaled by path-steps to the whole mix"}
+    res3["workload"] = "1024-contract batched mix (64-contract subset)"
+    out["batched_mix"] = res3
+    # config 4: the gradient (7 tangent directions) of the 252-step Asian call, 2^20 paths
+    c4 = oracle.Contract(1, 100.0, 1.0)
+    out["adjoint_gradient"] = rate(lambda n: oracle.mc_gradient(P2, c4, n, 252, w2.seed),
+                                   1 << 20, 252, "Asian call K=100, 252 steps, 2^20 paths, "
+                                   "d price / d (S0, v0, kappa, theta, xi, rho, r)", 1)
+    return out
 
 
 def cpu_baseline(target_s: float = 10.0):
@@ -267,13 +388,23 @@ def run_gpu(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    for _ in range(max(3, args.warmup)):
-        step()
-    barrier()
-
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
+    # measured issue rates of the pipes the kernels use: the roofline denominators
+    from paper_2309_10477_gb300 import peaks as pipe_peaks
+    pk = None
+    t_pk = (time.time(), time.time())
+    if not args.no_peaks:
+        clocks.mark(True)
+        t_pk = time.time()
+        pk = pipe_peaks.measure(args.peak_seconds, local)
+        t_pk = (t_pk, time.time())
+        clocks.mark(False)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    barrier()
     events = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     barrier()
     clocks.mark(True)
@@ -291,6 +422,88 @@ def run_gpu(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     ms, k1 = float(t[0]), float(t[1])
     estimates = out.view(nc, 12).cpu().numpy()
+
+    # one estimate split across the ranks (strong scaling next to the replica number):
+    # each rank simulates its path range of the 2^22 paths, the tile rows are
+    # all-gathered over NCCL and reduced in the fixed order -- all inside the timing
+    sharded = None
+    if world > 1 and not args.no_sharded:
+        from paper_2309_10477_gb300 import parallel
+        n_all = w.n_paths
+        sopts = nv.make_options(prec=nv.HESTON_FP32, stream=stream, device=local)
+        for _ in range(2):
+            parallel.price_greeks_sharded(params, contracts, n_all, w.n_steps, w.seed, sopts)
+        barrier()
+        sh_times = []
+        res_sh = None
+        for i in range(max(3, min(args.steps, 20))):
+            flush.fill_(i & 0xFF)
+            barrier()
+            t0 = time.perf_counter()
+            res_sh = parallel.price_greeks_sharded(params, contracts, n_all, w.n_steps, w.seed, sopts)
+            torch.cuda.synchronize()
+            sh_times.append(time.perf_counter() - t0)
+        tt = torch.tensor([statistics.mean(sh_times)], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        same = None
+        if rank == 0:                          # the same estimate on this GPU alone
+            ws_all_bytes = nv.heston_mc_workspace_bytes(nc, n_all)
+            ws_all = torch.empty(ws_all_bytes // 8 + 32, dtype=torch.float64, device=dev)
+            out_all = torch.empty(nc * 12, dtype=torch.float64, device=dev)
+            nv.heston_mc_launch(params, contracts, n_all, w.n_steps, w.seed, sopts, ws_all,
+                                ws_all_bytes, out_all)
+            torch.cuda.synchronize()
+            same = bool(torch.equal(out_all.view(nc, 12).cpu(), res_sh))
+        barrier()
+        sh_s = float(tt[0])
+        sharded = {"workload": f"{w.name}: one estimate, the paths split across {world} ranks",
+                   "scaling": "strong", "ms_per_estimate": sh_s * 1e3,
+                   "path_steps_per_s": n_all * w.n_steps / sh_s,
+                   "greek_sets_per_s": nc / sh_s,
+                   "exchange": "NCCL all_gather of the 64-path tile rows, fixed-order reduction",
+                   "identical_to_one_gpu": same,
+                   "timing": "host clock around each estimate (launch, gather, reduce, result on the "
+                             "host), barrier before each, max over ranks"}
+
+    # config 1: one European call, 2^16 paths x 100 steps, FP64 path (FP64-pipe bound)
+    fp64v = None
+    if not args.no_fp64 and world == 1:
+        w1 = wl.single_european_fp64()
+        p1 = nv.make_params(**w1.params)
+        c1 = [nv.make_contract(*c) for c in w1.contracts]
+        ws1_bytes = nv.heston_mc_workspace_bytes(1, w1.n_paths)
+        ws1 = torch.empty(ws1_bytes // 8 + 32, dtype=torch.float64, device=dev)
+        out1 = torch.empty(12, dtype=torch.float64, device=dev)
+        o1 = nv.make_options(prec=nv.HESTON_FP64, stream=stream, device=local)
+        for _ in range(3):
+            nv.heston_mc_launch(p1, c1, w1.n_paths, w1.n_steps, w1.seed, o1, ws1, ws1_bytes, out1)
+        barrier()
+        f_steps = max(5, min(args.steps, 50))
+        fev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(f_steps)]
+        clocks.mark(True)
+        for i in range(f_steps):
+            flush.fill_(i & 0xFF)
+            fev[i][0].record(stream)
+            nv.heston_mc_launch(p1, c1, w1.n_paths, w1.n_steps, w1.seed, o1, ws1, ws1_bytes, out1)
+            fev[i][1].record(stream)
+        barrier()
+        clocks.mark(False)
+        f_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in fev)
+        est1 = out1.view(1, 12).cpu().numpy()[0]
+        ps1 = w1.n_paths * w1.n_steps / (f_ms * 1e-3)
+        # measured DFMA rate; without the micro-benchmarks, 2 FP64 FMAs per SM per clock
+        dfma = (pk["dfma"]["thread_insts_per_s"] if pk else
+                2.0 * torch.cuda.get_device_properties(dev).multi_processor_count * 2070e6)
+        fp64v = {"workload": w1.name, "ms_per_step": f_ms, "path_steps_per_s": ps1,
+                 "greek_sets_per_s": 1.0 / (f_ms * 1e-3), "gpu_launches_per_step": 3,
+                 "estimates": dict(zip(nv.ESTIMATORS, est1[:6].tolist())),
+                 "se": dict(zip(nv.ESTIMATORS, est1[6:].tolist())),
+                 "roofline": {"bound": "fp64", "achieved": FP64_OPS_PER_PATH_STEP * ps1 / 1e12,
+                              "peak": dfma / 1e12, "frac": FP64_OPS_PER_PATH_STEP * ps1 / dfma,
+                              "unit": f"T FP64 operations/s ({FP64_OPS_PER_PATH_STEP} explicit FP64 "
+                                      "operations per path-step; the FP64 log, sqrt, sin/cos and "
+                                      "rsqrt run on the same pipe and are not counted; peak = the "
+                                      "measured DFMA rate)"}}
 
     # randomised-QMC variant on the same workload: 32 replicates x 2^17 points
     qmc = None
@@ -474,7 +687,7 @@ def run_gpu(args):
         gv = agrad.cpu().numpy()
         adjoint = {"workload": "Asian call K=100, 252 dates/steps, 2^20 paths, FP32 path / FP64 sums",
                    "forward_ms": statistics.mean(fwd), "backward_ms": statistics.mean(bwd),
-                   "checkpoint_every_steps": 16,
+                   "checkpoint_every_steps": 8,
                    "price": float(aprice[0]), "gradient": dict(zip(
                        ("S0", "v0", "kappa", "theta", "xi", "rho", "r"), gv[:7].tolist())),
                    "gradient_se": gv[7:].tolist()}
@@ -613,8 +826,14 @@ def run_gpu(args):
         n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
         clk = clocks.summary()
         max_mhz = float(peaks.get("sm_max_mhz") or clk.get("sm_max_mhz") or 2070.0)
-        peak_tinst = n_sm * ISSUE_LANES_PER_SM_CLK * max_mhz * 1e6 / 1e12
+        nominal_tinst = n_sm * ISSUE_LANES_PER_SM_CLK * max_mhz * 1e6 / 1e12
+        # measured: the FP32 FMA rate, one thread-instruction per lane per clock, the
+        # highest rate any instruction kind reaches (the machine's issue rate)
+        peak_tinst = (max(v["thread_insts_per_s"] for v in pk.values()) / 1e12 if pk
+                      else nominal_tinst)
         achieved_tinst = path_steps * ALGO_SLOTS_PER_PATH_STEP / (k1 * 1e-3) / 1e12
+        pk_clk = clocks.summary_between(*t_pk)
+        pk_mhz = pk_clk.get("sm_mhz") or max_mhz
         traffic = _profiled_traffic()
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -640,14 +859,29 @@ def run_gpu(args):
                          "achieved": achieved_tinst, "peak": peak_tinst,
                          "unit": f"T issue slots/s ({ALGO_SLOTS_PER_PATH_STEP} algorithmic slots per "
                                  f"path-step: {ALGO_OPS_PER_PATH_STEP} operations, FP32 ones packed "
-                                 f"two per f32x2 instruction; peak = {n_sm} SMs x 128 lanes x "
-                                 f"{max_mhz:.0f} MHz)",
+                                 "two per f32x2 instruction; peak = the measured issue rate, the "
+                                 "FP32 FMA micro-benchmark's thread-instructions/s)",
+                         "peak_source": ("measured (pipe_peaks, this run)" if pk else
+                                         "nominal: SMs x 128 lanes x max clock (--no-peaks)"),
+                         "nominal_peak": nominal_tinst,
                          "ops_per_s": path_steps * ALGO_OPS_PER_PATH_STEP / (k1 * 1e-3) / 1e12,
-                         "frac": achieved_tinst / peak_tinst, "traffic": traffic,
+                         "frac": achieved_tinst / peak_tinst,
+                         "frac_92_slot_model": path_steps * SCALAR_SLOTS_PER_PATH_STEP / (k1 * 1e-3)
+                         / 1e12 / peak_tinst,
+                         "traffic": traffic,
                          "kernel_ms": k1,
                          "path_steps_per_s_kernel": path_steps / (k1 * 1e-3)},
+            "pipe_peaks": None if pk is None else {
+                "unit": "T thread-instructions/s", "sm_mhz_median": pk_mhz,
+                "rates": {k: v["thread_insts_per_s"] / 1e12 for k, v in pk.items()},
+                "per_sm_per_clock": {k: v["thread_insts_per_s"] / (n_sm * pk_mhz * 1e6)
+                                     for k, v in pk.items()}},
             "clocks": clk,
         }
+        if fp64v is not None:
+            line["fp64_single_european_variant"] = fp64v
+        if sharded is not None:
+            line["sharded_variant"] = sharded
         if qmc is not None:
             line["qmc_variant"] = qmc
         if batched is not None:
@@ -660,6 +894,8 @@ def run_gpu(args):
             line["scheme_variants"] = schemes
         if not args.no_cpu_baseline and world == 1:      # the oracle baseline: rank 0 at N = 1 only
             line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+            line["cpu_baseline"]["host"] = host_info()
+            line["cpu_baselines_by_config"] = cpu_baselines(args.cpu_config_seconds)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
@@ -685,6 +921,15 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--serve-tiles-per-round", type=int, default=65536)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--cpu-config-seconds", type=float, default=2.0,
+                    help="oracle seconds per configuration and core mode")
+    ap.add_argument("--peak-seconds", type=float, default=0.3,
+                    help="timed seconds per instruction kind of the pipe micro-benchmarks")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 single-European variant")
+    ap.add_argument("--no-peaks", action="store_true",
+                    help="skip the pipe micro-benchmarks (roofline against the nominal peak; for ncu runs)")
+    ap.add_argument("--no-sharded", action="store_true",
+                    help="skip the estimate split across ranks (N > 1)")
     ap.add_argument("--n-paths", type=int, default=0,
                     help="paths per rank (default: the workload's 2^22); small cases for ncu")
     args = ap.parse_args()

@@ -1,4 +1,7 @@
-"""Build the in-tree CUDA library ``libhestonmc.so`` for sm_103a with nvcc."""
+"""Build the in-tree CUDA libraries for sm_103a with nvcc: ``libhestonmc.so``
+(the pricing path behind include/heston_mc.h) and ``libpipepeaks.so`` (the
+issue-rate micro-benchmarks that give the roofline denominators).  The two
+compile in parallel."""
 from __future__ import annotations
 
 import os
@@ -10,6 +13,8 @@ _ROOT = os.path.dirname(_HERE)
 SOURCES = [os.path.join(_HERE, "csrc", "heston_mc.cu")]
 HEADERS = [os.path.join(_ROOT, "include", "heston_mc.h"), os.path.join(_HERE, "csrc", "heston_device.cuh")]
 TARGET = os.path.join(_HERE, "libhestonmc.so")
+PEAKS_SOURCES = [os.path.join(_HERE, "csrc", "pipe_peaks.cu")]
+PEAKS_TARGET = os.path.join(_HERE, "libpipepeaks.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -20,19 +25,34 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found")
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    newest = max(os.path.getmtime(p) for p in SOURCES + HEADERS)
-    if not force and os.path.exists(TARGET) and os.path.getmtime(TARGET) >= newest:
-        return TARGET
-    tmp = TARGET + f".tmp{os.getpid()}"
+def _stale(target, deps):
+    return not os.path.exists(target) or os.path.getmtime(target) < max(os.path.getmtime(p) for p in deps)
+
+
+def _cmd(sources, tmp, verbose):
     cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
-           "-I", os.path.join(_ROOT, "include"), *SOURCES, "-o", tmp]
+           "-I", os.path.join(_ROOT, "include"), *sources, "-o", tmp]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError("nvcc failed:\n" + r.stderr[-4000:])
-    os.replace(tmp, TARGET)
+    return cmd
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    jobs = []
+    for sources, deps, target in ((SOURCES, SOURCES + HEADERS, TARGET),
+                                  (PEAKS_SOURCES, PEAKS_SOURCES, PEAKS_TARGET)):
+        if force or _stale(target, deps):
+            tmp = target + f".tmp{os.getpid()}"
+            p = subprocess.Popen(_cmd(sources, tmp, verbose), stdout=subprocess.PIPE,
+                                 stderr=subprocess.PIPE, text=True)
+            jobs.append((p, tmp, target))
+    for p, tmp, target in jobs:
+        out, err = p.communicate()
+        if p.returncode != 0:
+            raise RuntimeError(f"nvcc failed for {os.path.basename(target)}:\n" + err[-4000:])
+        if verbose:
+            print(err)
+        os.replace(tmp, target)
     return TARGET
 
 
