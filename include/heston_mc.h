@@ -23,6 +23,11 @@
  *   - Calls on different streams may run concurrently from different host
  *     threads; the library holds no global mutable state apart from the
  *     static scratch array of heston_mc_launch_noalloc.
+ *   - Per-device handles are cached for the life of the process: the
+ *     scratch memory pool of the synchronous entry points and the device
+ *     address of the static scratch array.  cudaDeviceReset invalidates
+ *     them, so a process must not call the library on a device after
+ *     resetting it.
  *
  * Random numbers (the contract both the GPU path and the test oracle
  * implement): Philox4x32-10 (Salmon et al., SC'11) with key = rng_seed
@@ -209,8 +214,10 @@ int heston_mc_launch(const heston_params *params, const heston_contract *contrac
  * n_contracts x 12 doubles (layout as for heston_mc_launch).
  *   - Calls no cudaMalloc, cudaFree or other allocating routine.
  *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture on the device.
+ *     (cudaGetSymbolAddress) with that device current and caches it for the
+ *     process; make that first call before any stream capture on the
+ *     device, and make no call on a device after cudaDeviceReset on it (the
+ *     cached address would be stale).
  *   - A request larger than HESTON_NOALLOC_SCRATCH_BYTES returns
  *     HESTON_ERR_WORKSPACE and launches nothing; other errors as for
  *     heston_mc_launch (HESTON_ERR_INVALID_ARG also for d_out == NULL).
@@ -455,9 +462,9 @@ int heston_server_destroy(heston_server *s);
  * Milstein recursion with full truncation.  FP32 paths, FP64 sums, Philox
  * normals, n_steps <= 1024; other options return HESTON_ERR_UNSUPPORTED.
  * The forward call prices the contract and stores, per path, (X, V) every
- * C = ceil(sqrt(n_steps)) steps and the payoff slope; the backward call
- * rebuilds each C-step segment from its checkpoint (normals recomputed from
- * their Philox counters) and runs the adjoint sweep.  Both are asynchronous
+ * 8 steps and the payoff slope; the backward call rebuilds each 8-step
+ * segment from its checkpoint (normals recomputed from their Philox
+ * counters) in registers and runs the adjoint sweep.  Both are asynchronous
  * on opts->cuda_stream, allocate nothing, and must use the same workspace,
  * inputs and seed, the backward after the forward.
  *   d_workspace: device, 256-byte aligned, >= heston_adjoint_workspace_bytes.
@@ -474,6 +481,18 @@ int heston_mc_adjoint_backward(const heston_params *params, const heston_contrac
                                uint64_t n_paths, uint32_t n_steps, uint64_t rng_seed,
                                const heston_options *opts, void *d_workspace, size_t workspace_bytes,
                                double *d_grad);
+
+/* Test support: the per-path values of the adjoint kernels for paths
+ * 0 .. n_paths-1 (forward and backward enqueued on opts->cuda_stream, as
+ * above).  d_per_path: device, n_paths x 8 doubles per path: the discounted
+ * payoff, then its derivatives with respect to (S0, v0, kappa, theta, xi,
+ * rho, r) -- the FP32 values the estimates sum.  d_workspace must hold
+ * heston_adjoint_workspace_bytes + 768 bytes (the estimates are written
+ * past the workspace proper and not returned); HESTON_ERR_WORKSPACE if not. */
+int heston_mc_adjoint_debug_paths(const heston_params *params, const heston_contract *contract,
+                                  uint64_t n_paths, uint32_t n_steps, uint64_t rng_seed,
+                                  const heston_options *opts, void *d_workspace, size_t workspace_bytes,
+                                  double *d_per_path);
 
 /* ---- test support --------------------------------------------------------- */
 

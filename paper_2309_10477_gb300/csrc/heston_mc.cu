@@ -299,7 +299,7 @@ cudaError_t launch_paths_t(const Prepared &pp, const Coef<R> &k, const Launch &a
     int n_sm = 0;
     e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    const int block = pp.opt.block_threads ? (int)pp.opt.block_threads : kPathBlock;
+    int block = pp.opt.block_threads ? (int)pp.opt.block_threads : kPathBlock;
     uint64_t grid;
     if (pp.opt.grid_ctas) {
         grid = pp.opt.grid_ctas;
@@ -308,9 +308,22 @@ cudaError_t launch_paths_t(const Prepared &pp, const Coef<R> &k, const Launch &a
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, 0);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) per_sm = 1;
-        const uint64_t warps_per_cta = (uint64_t)block / 32;
-        const uint64_t need = (a.n_tiles + warps_per_cta - 1) / warps_per_cta;
-        const uint64_t full = (uint64_t)n_sm * (uint64_t)per_sm;
+        uint64_t warps_per_cta = (uint64_t)block / 32;
+        uint64_t need = (a.n_tiles + warps_per_cta - 1) / warps_per_cta;
+        uint64_t full = (uint64_t)n_sm * (uint64_t)per_sm;
+        // A launch that does not fill the machine gets one-warp CTAs, so that its
+        // tiles spread evenly over the SMs (4-warp CTAs leave some SMs one CTA
+        // and others two).  Tile rows do not depend on the shape.
+        if (!pp.opt.block_threads && need < full) {
+            int per_sm1 = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm1, kern, 32, 0);
+            if (e != cudaSuccess) return e;
+            if (per_sm1 < 1) per_sm1 = 1;
+            block = 32;
+            warps_per_cta = 1;
+            need = a.n_tiles;
+            full = (uint64_t)n_sm * (uint64_t)per_sm1;
+        }
         grid = need < full ? need : full;
     }
     if (grid < 1) grid = 1;
@@ -660,9 +673,11 @@ cudaError_t launch_qmc_t(const Prepared &pp, const QmcLaunch &a, cudaStream_t st
 {
     auto kern = heston_qmc_kernel<TRUNC, MON>;
     const int block = pp.opt.block_threads ? (int)pp.opt.block_threads : kPathBlock;
-    // the bridge plan and one row of D high-bit words per warp in shared memory
+    // the bridge plan, one row of D high-bit words per warp and (16-byte aligned)
+    // one bridge stack of depth x 32 float4 per warp in shared memory
     const size_t smem = (size_t)a.n_ev * sizeof(BridgeOp) + (size_t)((a.N + 4u) & ~3u) * sizeof(int32_t)
-                        + (size_t)(block / 32) * a.D * sizeof(uint32_t);
+                        + (size_t)(block / 32) * a.D * sizeof(uint32_t) + 16u
+                        + (size_t)(block / 32) * a.depth * 32u * sizeof(float4);
     int dev = 0, n_sm = 0, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
@@ -694,6 +709,7 @@ int enqueue_qmc(const Prepared &pp, uint64_t n_paths, uint64_t seed, const void 
     QmcLaunch a;
     a.tb = qmc_tables_at(d_tables, TL);
     a.n_ev = (uint32_t)plan.ev.size();
+    a.depth = (uint32_t)plan.depth;
     a.D = 2u * pp.N;
     a.N = pp.N;
     a.n_tiles = tiles_for(n_paths);
@@ -929,8 +945,7 @@ struct AdjLayout {
 AdjLayout adj_layout(uint64_t n_paths, uint32_t N)
 {
     AdjLayout L;
-    L.C = (uint32_t)std::ceil(std::sqrt((double)N));
-    if (L.C < 1) L.C = 1;
+    L.C = (uint32_t)kAdjSeg;
     L.n_seg = (N + L.C - 1) / L.C;
     const uint64_t tiles = tiles_for(n_paths);
     L.off_ckpt = 0;
@@ -948,27 +963,22 @@ cudaError_t launch_adj_t(bool backward, const Prepared &pp, const AdjLaunch &a, 
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    const bool small = a.C <= 16u;
-    if (backward) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                      &per_sm, small ? heston_adj_bwd_kernel<MON, 16> : heston_adj_bwd_kernel<MON, kAdjMaxSeg>,
-                      kPathBlock, 0);
+    if (backward) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, heston_adj_bwd_kernel<MON>,
+                                                                    kPathBlock, 0);
     else          e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, heston_adj_fwd_kernel<MON>, kPathBlock, 0);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     uint64_t grid = std::min<uint64_t>((a.n_tiles + 3) / 4, (uint64_t)n_sm * per_sm);
     if (pp.opt.grid_ctas) grid = pp.opt.grid_ctas;
     if (grid < 1) grid = 1;
-    if (backward && small)
-        heston_adj_bwd_kernel<MON, 16><<<(unsigned)grid, kPathBlock, 0, st>>>(pp.kf, pp.csf, a, (float)pp.cs.T);
-    else if (backward)
-        heston_adj_bwd_kernel<MON, kAdjMaxSeg><<<(unsigned)grid, kPathBlock, 0, st>>>(pp.kf, pp.csf, a, (float)pp.cs.T);
+    if (backward) heston_adj_bwd_kernel<MON><<<(unsigned)grid, kPathBlock, 0, st>>>(pp.kf, pp.csf, a, (float)pp.cs.T);
     else          heston_adj_fwd_kernel<MON><<<(unsigned)grid, kPathBlock, 0, st>>>(pp.kf, pp.csf, a);
     return cudaGetLastError();
 }
 
 int adjoint_enqueue(bool backward, const heston_params *params, const heston_contract *contract,
                     uint64_t n_paths, uint32_t N, uint64_t seed, const heston_options *opts,
-                    void *ws, size_t ws_bytes, double *d_out)
+                    void *ws, size_t ws_bytes, double *d_out, double *d_per_path = nullptr)
 {
     Prepared pp;
     int rc = validate_and_prepare(params, contract, 1, n_paths, N, opts, pp);
@@ -977,7 +987,7 @@ int adjoint_enqueue(bool backward, const heston_params *params, const heston_con
         pp.opt.scheme != HESTON_SCHEME_MILSTEIN)
         return HESTON_ERR_UNSUPPORTED;
     const AdjLayout L = adj_layout(n_paths, N);
-    if (L.C > (uint32_t)kAdjMaxSeg) return HESTON_ERR_UNSUPPORTED;
+    if (N > kAdjMaxSteps) return HESTON_ERR_UNSUPPORTED;
     if (!d_out) return HESTON_ERR_INVALID_ARG;
     if (!ws || ((uintptr_t)ws & 255u) || ws_bytes < L.total) return HESTON_ERR_WORKSPACE;
     DeviceGuard g(pp.opt.device);
@@ -994,6 +1004,7 @@ int adjoint_enqueue(bool backward, const heston_params *params, const heston_con
     a.ckpt = (float2 *)(b + L.off_ckpt);
     a.seed = (float2 *)(b + L.off_seed);
     a.rows = (double *)(b + L.off_rows);
+    a.per_path = d_per_path;
     const int mon = mon_mode(pp.cs);
     cudaError_t e = mon == MON_NONE ? launch_adj_t<MON_NONE>(backward, pp, a, st)
                   : mon == MON_EVERY ? launch_adj_t<MON_EVERY>(backward, pp, a, st)
@@ -1692,8 +1703,8 @@ int heston_mc_price_greeks_batch(const heston_batch_item *items, uint32_t n_item
 int heston_adjoint_workspace_bytes(uint64_t n_paths, uint32_t n_steps, size_t *bytes)
 {
     if (!bytes || n_paths < 2 || n_paths > (1ull << 40) || n_steps == 0) return HESTON_ERR_INVALID_ARG;
+    if (n_steps > kAdjMaxSteps) return HESTON_ERR_UNSUPPORTED;
     const AdjLayout L = adj_layout(n_paths, n_steps);
-    if (L.C > (uint32_t)kAdjMaxSeg) return HESTON_ERR_UNSUPPORTED;
     *bytes = L.total;
     return HESTON_OK;
 }
@@ -1714,6 +1725,30 @@ int heston_mc_adjoint_backward(const heston_params *params, const heston_contrac
 {
     return adjoint_enqueue(true, params, contract, n_paths, n_steps, rng_seed, opts, d_workspace,
                            workspace_bytes_, d_grad);
+}
+
+int heston_mc_adjoint_debug_paths(const heston_params *params, const heston_contract *contract,
+                                  uint64_t n_paths, uint32_t n_steps, uint64_t rng_seed,
+                                  const heston_options *opts, void *d_workspace, size_t workspace_bytes_,
+                                  double *d_per_path)
+{
+    if (!d_per_path) return HESTON_ERR_INVALID_ARG;
+    Prepared pp;
+    int rc = validate_and_prepare(params, contract, 1, n_paths, n_steps, opts, pp);
+    if (rc < 0) return rc;
+    // price (2 doubles) and gradient (14) past the workspace proper: at most 255
+    // bytes of alignment + 256 + 112 <= 768
+    if (!d_workspace || workspace_bytes_ < adj_layout(n_paths, n_steps).total + 768u)
+        return HESTON_ERR_WORKSPACE;
+    // the estimates go to the end of the workspace; only the per-path values are returned
+    char *tail = (char *)d_workspace + adj_layout(n_paths, n_steps).total;
+    double *d_price = (double *)(((uintptr_t)tail + 255u) & ~(uintptr_t)255u);
+    double *d_grad = d_price + 32;
+    const size_t ws = adj_layout(n_paths, n_steps).total;
+    rc = adjoint_enqueue(false, params, contract, n_paths, n_steps, rng_seed, opts, d_workspace, ws, d_price);
+    if (rc < 0) return rc;
+    return adjoint_enqueue(true, params, contract, n_paths, n_steps, rng_seed, opts, d_workspace, ws, d_grad,
+                           d_per_path);
 }
 
 int heston_release_cached_memory(int32_t device)

@@ -142,6 +142,8 @@ def load():
                                        P(heston_options), vp, sz, vp], i32),
         "heston_mc_adjoint_backward": ([P(heston_params), P(heston_contract), u64, u32, u64,
                                         P(heston_options), vp, sz, vp], i32),
+        "heston_mc_adjoint_debug_paths": ([P(heston_params), P(heston_contract), u64, u32, u64,
+                                           P(heston_options), vp, sz, vp], i32),
         "heston_release_cached_memory": ([i32], i32),
         "heston_server_create": ([P(heston_server_config), P(vp)], i32),
         "heston_server_submit": ([vp, P(heston_batch_item), P(u64)], i32),
@@ -410,6 +412,13 @@ def heston_mc_adjoint_backward(params, contract, n_paths, n_steps, rng_seed, opt
     return _check(load().heston_mc_adjoint_backward(ctypes.byref(params), ctypes.byref(contract),
                                                     n_paths, n_steps, rng_seed, ctypes.byref(options),
                                                     _ptr(workspace), workspace_bytes, _ptr(grad)))
+
+
+def heston_mc_adjoint_debug_paths(params, contract, n_paths, n_steps, rng_seed, options, workspace,
+                                  workspace_bytes, per_path) -> int:
+    return _check(load().heston_mc_adjoint_debug_paths(ctypes.byref(params), ctypes.byref(contract),
+                                                       n_paths, n_steps, rng_seed, ctypes.byref(options),
+                                                       _ptr(workspace), workspace_bytes, _ptr(per_path)))
 
 
 class HestonServer:
