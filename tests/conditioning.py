@@ -141,7 +141,13 @@ def path_scales(rec_o, est_o, params, contracts, n_steps):
     vs = max(params["theta"], params["v0"])
     sc[:, 1] = np.maximum(np.abs(rec_o[:, 1]), vs)
     sc[:, 5] = np.maximum(sc[:, 5], vs / contracts[0][2])
-    esc = np.maximum(np.abs(est_o), np.median(np.abs(est_o), axis=0))
+    # estimators: the median over the paths where the estimator is not zero (an
+    # out-of-the-money path contributes an exact zero, not a typical size)
+    a = np.abs(est_o)
+    nz = np.where(a > 0, a, np.nan)
+    with np.errstate(all="ignore"):
+        med = np.nan_to_num(np.nanmedian(nz, axis=0), nan=0.0)
+    esc = np.maximum(a, med)
     for ci, c in enumerate(contracts):
         A = params["S0"] * np.exp(rec_o[:, 0]) if c[0] == 0 else rec_o[:, 6] / (c[4] or n_steps)
         esc[:, ci, 0] = np.maximum(esc[:, ci, 0], np.maximum(A, c[1]))

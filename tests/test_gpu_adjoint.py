@@ -32,8 +32,7 @@ def _run(nv, torch, params, c, n, N, seed):
     return out.cpu().numpy(), g.cpu().numpy()
 
 
-# N = 300 and 1024 take the backward kernel's 32-step segment arrays (C = 18, 32);
-# the others the 16-step ones
+# segments of 8 steps: N = 7 and 300 end on a short segment, 1024 is the largest N
 @pytest.mark.parametrize("payoff,put,M,N,n", [(0, 0, 0, 64, 1 << 15), (1, 0, 0, 252, 1 << 14),
                                               (1, 1, 4, 32, (1 << 15) + 37), (0, 1, 0, 7, 5000),
                                               (1, 0, 0, 300, 4096 + 5), (0, 0, 0, 1024, 2048)])
@@ -87,7 +86,49 @@ def test_adjoint_rejections(nv):
         with pytest.raises(nv.HestonError) as e:
             nv.heston_mc_adjoint_forward(p, c, 1024, 10, 1, opts, ws, 8 << 20, out)
         assert e.value.status == nv.HESTON_ERR_UNSUPPORTED
-    for N in (1025, 2000):                       # segments of more than 32 steps
+    for N in (1025, 2000):                       # beyond the 1024-step limit
         with pytest.raises(nv.HestonError) as e:
             nv.heston_adjoint_workspace_bytes(1024, N)
         assert e.value.status == nv.HESTON_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("payoff,put,M,N,n", [(0, 0, 0, 64, 3000), (1, 0, 0, 252, 1500),
+                                              (1, 1, 4, 32, 700 + 37), (0, 1, 0, 7, 500)])
+def test_adjoint_per_path_against_the_oracle(nv, payoff, put, M, N, n):
+    """The adjoint kernels' per-path payoff and its 7 derivatives (the FP32
+    values the estimates sum) against the oracle's forward-mode gradient on
+    the same normals: within max(1e-5, 2 N 2^-24) of each component's scale
+    (max(|x|, the sample's median |x|); the payoff max(K, A)) plus four times the oracle's
+    own change under FP32-rounded inputs and normals moved within the FP32
+    normal-error bound.  Paths whose truncation branch or payoff indicator
+    can flip between FP32 and FP64 are counted, not compared."""
+    import torch
+    from conditioning import oracle_gradients_with_sensitivity
+    contract = (payoff, 100.0, 1.0, put, M)
+    c = nv.make_contract(*contract)
+    p = nv.make_params(**BASE)
+    ws_bytes = nv.heston_adjoint_workspace_bytes(n, N) + 768
+    ws = torch.empty(ws_bytes // 8 + 32, dtype=torch.float64, device="cuda")
+    per = torch.empty(n * 8, dtype=torch.float64, device="cuda")
+    opts = nv.make_options(prec=nv.HESTON_FP32, stream=torch.cuda.current_stream())
+    nv.heston_mc_adjoint_debug_paths(p, c, n, N, 23, opts, ws, ws_bytes, per)
+    torch.cuda.synchronize()
+    got = per.view(n, 8).cpu().numpy()
+    paths = np.arange(n, dtype=np.uint64)
+    og, dg = oracle_gradients_with_sensitivity(BASE, contract, paths, N, 23)
+    rec, _ = oracle.debug_paths(oracle.Params(**BASE), [oracle.Contract(*contract)], paths, N, 23)
+    A = BASE["S0"] * np.exp(rec[:, 0]) if payoff == 0 else rec[:, 6] / (M or N)
+    flips = (rec[:, 14] < 1e-5 * max(BASE["theta"], BASE["v0"])) | (np.abs(A - 100.0) < 2e-5 * 100.0)
+    assert flips.sum() <= max(2, n // 1000)
+    ok = ~flips
+    scale = np.maximum(np.abs(og), np.median(np.abs(og), axis=0))
+    scale[:, 0] = np.maximum(scale[:, 0], np.maximum(A, 100.0))
+    # each derivative comes out of two FP32 recursions over the N steps: the
+    # adjoint state (V-bar, X-bar, carried backwards) and the running sum of its
+    # contributions; their rounding bounds each grow like N u (u = 2^-24), so
+    # the tolerance is 1e-5 or 2 N u, the larger
+    rel = max(1e-5, 2.0 * N * 2.0 ** -24)
+    lim = rel * scale + 4.0 * dg
+    d = np.abs(got - og)
+    assert (d[ok] <= lim[ok]).all(), ((d / lim)[ok].max(axis=0), np.argwhere((d > lim) & ok[:, None])[:5])
+    assert (d[ok] > rel * scale[ok]).sum() <= 0.05 * ok.sum() * 8

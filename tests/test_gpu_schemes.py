@@ -2,26 +2,30 @@
 Philox normals, through the C ABI.
 
 Tolerances as for the Milstein path (tests/test_gpu_parity.py):
-  * per path, FP64: every record field and estimator within 1e-9 relative;
-    paths whose branch decision lies within 1e-9 * max(theta, v0) of its
-    threshold (a truncation sign, the QE switch psi = 1.5 or the QE zero
-    mass) are counted, not compared.
-  * per path, FP32: ln S_T, V_T and the payoff underlyings within 1e-5
-    relative (V relative to max(|V|, theta, v0)), discounted payoffs within
-    1e-5 * max(K, A); paths within 1e-5 * max(theta, v0) of a branch
-    decision, or with A within 2e-5 K of the strike, are counted, not
-    compared (at most 3 % of the sample: QE on a Feller-violating set meets
-    its zero-mass threshold often).
+  * per path, FP64: every record field and estimator within 1e-12 of its
+    scale (tests/conditioning.py path_scales) plus four times the oracle's
+    own change when its normals move by a few ulp; paths whose branch
+    decision lies within 1e-9 * max(theta, v0) of its threshold (a
+    truncation sign, the QE switch psi = 1.5 or the QE zero mass) are
+    counted, not compared.
+  * per path, FP32: every record field (ln S_T, V_T, tangents, Asian sums,
+    Gamma weights) and per-path estimator within 1e-5 of its scale plus four
+    times the oracle's own change under FP32-rounded inputs and normals
+    moved within the FP32 normal-error bound; paths within 1e-5 (QE) or 1e-4
+    (Euler) * max(theta, v0) of a branch decision, or with A within 2e-5 K
+    of the strike, are counted, not compared (at most 3 % of the sample: QE
+    on a Feller-violating set meets its zero-mass threshold often).
   * estimates: FP64 within 1e-9 relative; FP32 within 3 standard errors and
-    1e-4 * max(1, |oracle|), except Vega and Theta of a parameter set that
-    violates the Feller condition (2 kappa theta < xi^2): their per-path
-    tangents pass through 1/(2 sqrt(V)) near V = 0, which amplifies FP32
-    rounding, so they are held to the 3 standard errors only.
+    1e-4 * max(1, |oracle|) wherever the estimate is well-conditioned at FP32
+    precision (tests/conditioning.py: the oracle's own change under
+    FP32-sized perturbations stays below a third of the bound).
 """
 import numpy as np
 import pytest
 
 import oracle
+from conditioning import (check_fp32_estimates, check_paths, oracle_paths_with_sensitivity,
+                          oracle_with_sensitivity)
 from paper_2309_10477_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
@@ -71,13 +75,11 @@ def test_per_path_fp64(nv, name, scheme, trunc, pname, params, N):
     paths = _paths()
     opts = nv.make_options(trunc=trunc, prec=nv.HESTON_FP64, scheme=scheme)
     rec_g, est_g = nv.heston_mc_debug_paths(_gp(nv, params), _gc(nv, CS), N, 42, opts, paths)
-    rec_o, est_o = oracle.debug_paths(oracle.Params(**params), _oc(CS), paths, N, 42, trunc, scheme)
-    scale = np.maximum(1.0, np.abs(rec_o[:, :14]))
-    bad = (np.abs(rec_g[:, :14] - rec_o[:, :14]) > 1e-9 * scale).any(axis=1)
-    bad |= (np.abs(est_g - est_o) > 1e-9 * np.maximum(1.0, np.abs(est_o))).any(axis=(1, 2))
-    flips = bad & (rec_o[:, 14] < 1e-9 * max(params["theta"], params["v0"]))
-    assert (bad & ~flips).sum() == 0, np.nonzero(bad & ~flips)[0][:5]
+    rec_o, est_o, drec, dest = oracle_paths_with_sensitivity(params, CS, paths, N, 42, trunc, scheme,
+                                                             prec="fp64")
+    flips = rec_o[:, 14] < 1e-9 * max(params["theta"], params["v0"])
     assert flips.sum() <= 1
+    check_paths(rec_g, est_g, rec_o, est_o, drec, dest, params, CS, N, ~flips, 1e-12, name)
 
 
 @pytest.mark.parametrize("name,scheme,trunc", SCHEMES)
@@ -87,7 +89,7 @@ def test_per_path_fp32(nv, name, scheme, trunc, pname, params, N):
     paths = _paths()
     opts = nv.make_options(trunc=trunc, prec=nv.HESTON_FP32, scheme=scheme)
     rec_g, est_g = nv.heston_mc_debug_paths(_gp(nv, params), _gc(nv, CS), N, 42, opts, paths)
-    rec_o, est_o = oracle.debug_paths(oracle.Params(**params), _oc(CS), paths, N, 42, trunc, scheme)
+    rec_o, est_o, drec, dest = oracle_paths_with_sensitivity(params, CS, paths, N, 42, trunc, scheme)
     vs = max(params["theta"], params["v0"])
     # Paths near a branch decision are counted, not compared.  Euler: within
     # eps of V = 0, sqrt(V) turns an FP32 rounding error d in V into an error of
@@ -99,18 +101,22 @@ def test_per_path_fp32(nv, name, scheme, trunc, pname, params, N):
     band = 1e-5 if scheme == nv.HESTON_SCHEME_QE else 1e-4
     flips = (rec_o[:, 14] < band * vs) | _near_strike(rec_o, CS, params["S0"], N, 2e-5)
     assert flips.sum() <= max(2, 0.03 * len(paths)), flips.sum()
-    ok = ~flips
-    X_g, X_o = rec_g[ok, 0], rec_o[ok, 0]
-    errX = np.abs(X_g - X_o) / np.maximum(1.0, np.abs(X_o))
-    assert (errX <= 1e-5).all(), errX.max()
-    errV = np.abs(rec_g[ok, 1] - rec_o[ok, 1]) / np.maximum(np.abs(rec_o[ok, 1]), vs)
-    assert (errV <= 1e-5).all(), errV.max()
-    S0 = params["S0"]
-    for g, o in ((S0 * np.exp(X_g), S0 * np.exp(X_o)), (rec_g[ok, 6], rec_o[ok, 6])):
-        assert (np.abs(g - o) <= 1e-5 * np.abs(o)).all()
-    for ci, c in enumerate(CS):
-        A = np.maximum(c[1], np.abs(est_o[ok, ci, 1]) * S0)
-        assert (np.abs(est_g[ok, ci, 0] - est_o[ok, ci, 0]) <= 1e-5 * np.maximum(A, 1.0)).all()
+    # every record field and per-path estimator: 1e-5 of its scale plus four
+    # times the oracle's own change under FP32-sized perturbations.  QE's
+    # v0- and T-tangents differentiate psi = s^2 / m^2, whose derivative
+    # subtracts two nearly equal terms (s^2_v / s^2 and 2 m_v / m both follow
+    # V_v): the cancellation amplifies the FP32 rounding of the tangent
+    # formulas themselves, which perturbing the inputs does not model; those
+    # fields (X_v, V_v, X_T, V_T, the Asian tangent sums, Vega, Theta) are
+    # held to 5e-5 of their scale (measured: up to 2.1e-5)
+    rel = 1e-5
+    if scheme == nv.HESTON_SCHEME_QE:
+        rel = np.full(14, 1e-5)
+        rel[[2, 3, 4, 5, 8, 9]] = 5e-5
+        rel_e = np.array([1e-5, 1e-5, 1e-5, 5e-5, 1e-5, 5e-5])
+        rel = (rel, rel_e)
+    n_wide = check_paths(rec_g, est_g, rec_o, est_o, drec, dest, params, CS, N, ~flips, rel, name)
+    assert n_wide <= 0.05 * (~flips).sum() * (14 + 6 * len(CS)), n_wide
 
 
 def _gpu_estimates(nv, params, cs, n, N, seed, prec, trunc, scheme):
@@ -132,22 +138,19 @@ def test_estimates_fp64_match_oracle(nv, name, scheme, trunc, n, N):
 @pytest.mark.parametrize("name,scheme,trunc", SCHEMES)
 @pytest.mark.parametrize("params", [BASE, PAPER], ids=["base", "paper"])
 def test_estimates_fp32_match_oracle(nv, name, scheme, trunc, params):
+    """Within 3 SE and 1e-4 of the FP64 oracle wherever the estimate is
+    well-conditioned at FP32 precision (tests/conditioning.py).  On the
+    paper's Feller-violating set the Euler and QE Vega and Theta are not:
+    the oracle's own values move by more than a third of the bound under
+    FP32-sized perturbations (Euler, with no Milstein term, reaches V < 0
+    often enough for its Vega to come close even on the base set).  Price,
+    Delta, Gamma and Rho are well-conditioned everywhere here."""
     w = wl.multi_strike_fp32(1 << 16)
     gm, gse = _gpu_estimates(nv, params, w.contracts, w.n_paths, w.n_steps, 3, nv.HESTON_FP32,
                              trunc, scheme)
-    om, ose = oracle.mc_price_greeks(oracle.Params(**params), _oc(w.contracts), w.n_paths,
-                                     w.n_steps, 3, trunc, scheme=scheme)
-    # Vega/Theta of a Feller-violating set carry unbounded per-path tangents
-    # (HESTON_WARN_TANGENT_UNSTABLE); compare them only where both are finite
-    fin = np.isfinite(gm) & np.isfinite(om)
-    d = np.abs(gm - om)
-    assert (d[fin] <= 3 * ose[fin]).all(), np.max(d[fin] / ose[fin])
-    tight = fin.copy()
-    if 2 * params["kappa"] * params["theta"] < params["xi"] ** 2:
-        tight[:, [3, 5]] = False
-    assert (d[tight] <= 1e-4 * np.maximum(1.0, np.abs(om[tight]))).all(), \
-        np.max(d[tight] / np.maximum(1.0, np.abs(om[tight])))
-    assert fin[:, [0, 1, 2, 4]].all()
+    om, ose, delta = oracle_with_sensitivity(params, w.contracts, w.n_paths, w.n_steps, 3, trunc, scheme)
+    ill = check_fp32_estimates(gm, om, ose, delta, name)
+    assert not ill[:, [0, 1, 2, 4]].any()            # price, Delta, Gamma, Rho always well-conditioned here
 
 
 @pytest.mark.parametrize("scheme", [1, 2])
