@@ -60,6 +60,13 @@ ISSUE_LANES_PER_SM_CLK = 128          # 4 SM sub-partitions x 1 warp-instruction
 # functions (log, sqrt, sin and cos of 2 pi u2, 1 / sqrt(V dt)) that run on
 # the same pipe and are not counted.
 FP64_OPS_PER_PATH_STEP = 47
+# The FMA pipe's heavy half, which binds the FP32 path kernel: per warp and
+# lane-step (32 lanes x 2 paths = 64 path-steps) the lane's 20 Philox wide
+# multiplies take about 4 of its cycles each and its 48 f32x2 FMA-pipe
+# instructions 2 each (pipe micro-benchmarks): 176 cycles, one heavy half per
+# SM sub-partition.
+HEAVY_CYCLES_PER_LANE_STEP = 176
+HEAVY_LANE_STEP_PATHS = 64
 FLUSH_BYTES = 256 << 20               # > 129 MB L2
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "heston_paths_kernel_multi_strike_2p22.md")
 KERNEL_SOURCE = os.path.join(ROOT, "paper_2309_10477_gb300", "csrc", "heston_device.cuh")
@@ -153,6 +160,23 @@ class ClockSampler:
 
 def _source_hash():
     return hashlib.sha256(open(KERNEL_SOURCE, "rb").read()).hexdigest()[:16]
+
+
+FP64_PROFILE = os.path.join(ROOT, "profiles", "heston_paths_kernel_fp64_single_european_2p16.md")
+
+
+def _profile_value(path, pattern):
+    """A number from a committed ncu summary, or None if the device source
+    changed since it was captured."""
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"source sha256\[:16\]:\s*([0-9a-f]{16})", text)
+    v = re.search(pattern, text)
+    if not m or not v or m.group(1) != _source_hash():
+        return None
+    return float(v.group(1))
 
 
 def _profiled_traffic():
@@ -504,6 +528,13 @@ def run_gpu(args):
                                       "operations per path-step; the FP64 log, sqrt, sin/cos and "
                                       "rsqrt run on the same pipe and are not counted; peak = the "
                                       "measured DFMA rate)"}}
+        # from the committed ncu summary of this kernel (None once the device source changed)
+        busy = _profile_value(FP64_PROFILE, r"sm__pipe_fp64_cycles_active \(of elapsed\)\*\* \| \*\*([0-9.]+) %")
+        executed = _profile_value(FP64_PROFILE, r"DADD [0-9.]+: ([0-9.]+) arithmetic")
+        fp64v["roofline"]["fp64_pipe_busy_ncu"] = None if busy is None else busy / 100.0
+        fp64v["roofline"]["executed_fp64_per_path_step_ncu"] = executed
+        if executed is not None:
+            fp64v["roofline"]["frac_executed"] = executed * ps1 / dfma
 
     # randomised-QMC variant on the same workload: 32 replicates x 2^17 points
     qmc = None
@@ -872,6 +903,18 @@ def run_gpu(args):
                          "frac_92_slot_model": path_steps * SCALAR_SLOTS_PER_PATH_STEP / (k1 * 1e-3)
                          / 1e12 / peak_tinst,
                          "traffic": traffic,
+                         "binding_pipe": {
+                             "pipe": "fmaheavy (the FMA pipe's heavy half)",
+                             "busy_ncu": (None if (hb := _profile_value(
+                                 PROFILE_SUMMARY, r"sm__pipe_fmaheavy_cycles_active \(of elapsed\) \| \*\*([0-9.]+) %"))
+                                 is None else hb / 100.0),
+                             "model": "per warp and lane-step (64 path-steps): 20 Philox wide multiplies x 4 "
+                                      "heavy-pipe cycles + 48 f32x2 FMA-pipe instructions x 2 = 176 cycles",
+                             "ceiling_path_steps_per_s": HEAVY_LANE_STEP_PATHS * 4 * n_sm
+                             * (pk_mhz or max_mhz) * 1e6 / HEAVY_CYCLES_PER_LANE_STEP,
+                             "frac": (path_steps / (k1 * 1e-3)) / (HEAVY_LANE_STEP_PATHS * 4 * n_sm
+                                                                  * (pk_mhz or max_mhz) * 1e6
+                                                                  / HEAVY_CYCLES_PER_LANE_STEP)},
                          "kernel_ms": k1,
                          "path_steps_per_s_kernel": path_steps / (k1 * 1e-3)},
             "pipe_peaks": None if pk is None else {

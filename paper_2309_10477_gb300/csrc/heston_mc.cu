@@ -645,7 +645,7 @@ QmcLayout qmc_layout(uint32_t N, size_t n_ev)
     QmcLayout L;
     L.off_V = 0;
     L.off_T = align256(L.off_V + D * 32 * sizeof(uint32_t));
-    L.off_evoff = align256(L.off_T + D * 64 * sizeof(uint32_t));
+    L.off_evoff = align256(L.off_T + D * 64 * sizeof(uint32_t));     // N nodes x 32 lanes x uint4
     L.off_ev = align256(L.off_evoff + (N + 1) * sizeof(int32_t));
     L.total = align256(L.off_ev + n_ev * sizeof(BridgeOp));
     return L;
@@ -654,7 +654,7 @@ QmcLayout qmc_layout(uint32_t N, size_t n_ev)
 QmcTables qmc_tables_at(const void *base, const QmcLayout &L)
 {
     const char *b = (const char *)base;
-    return QmcTables{(const uint32_t *)(b + L.off_V), (const uint32_t *)(b + L.off_T),
+    return QmcTables{(const uint32_t *)(b + L.off_V), (const uint4 *)(b + L.off_T),
                      (const BridgeOp *)(b + L.off_ev), (const int32_t *)(b + L.off_evoff)};
 }
 
@@ -773,12 +773,13 @@ int build_qmc_tables(uint32_t N, void *d_tables, size_t bytes)
     uint32_t *V = (uint32_t *)(h.data() + L.off_V);
     uint32_t *T = (uint32_t *)(h.data() + L.off_T);
     sobol_directions_host(D, V);
+    // interleaved per bridge node j and lane l: x_{2j}(l), x_{2j}(l + 32), x_{2j+1}(l), x_{2j+1}(l + 32)
     for (uint32_t d = 0; d < D; ++d)
         for (uint32_t p = 0; p < 64; ++p) {
             uint32_t x = 0;
             for (int b = 0; b < 6; ++b)
                 if ((p >> b) & 1u) x ^= V[d * 32u + b];
-            T[d * 64u + p] = x;
+            T[((d >> 1) * 32u + (p & 31u)) * 4u + (d & 1u) * 2u + (p >> 5)] = x;
         }
     std::memcpy(h.data() + L.off_evoff, plan.off.data(), plan.off.size() * sizeof(int32_t));
     std::memcpy(h.data() + L.off_ev, plan.ev.data(), plan.ev.size() * sizeof(BridgeOp));
