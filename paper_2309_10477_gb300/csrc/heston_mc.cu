@@ -696,7 +696,7 @@ cudaError_t launch_qmc_t(const Prepared &pp, const QmcLaunch &a, cudaStream_t st
     const int block = pp.opt.block_threads ? (int)pp.opt.block_threads : kPathBlock;
     // the bridge plan, one row of D high-bit words per warp and (16-byte aligned)
     // one bridge stack of depth x 32 float4 per warp in shared memory
-    const size_t smem = (size_t)a.n_ev * sizeof(BridgeOp) + (size_t)((a.N + 4u) & ~3u) * sizeof(int32_t)
+    const size_t smem = (size_t)(a.n_ev + 1u) * sizeof(BridgeOp) + (size_t)((a.N + 4u) & ~3u) * sizeof(int32_t)
                         + (size_t)(block / 32) * a.D * sizeof(uint32_t) + 16u
                         + (size_t)(block / 32) * a.depth * 32u * sizeof(float4);
     int dev = 0, n_sm = 0, per_sm = 0;
