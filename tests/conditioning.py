@@ -92,30 +92,25 @@ def check_fp32_estimates(gm, om, ose, delta, label=""):
 FP64_NORMAL_REL = 1e-15   # FP64 Box-Muller: a few ulp of CUDA's log / sincospi against the C library's
 
 
-def oracle_paths_with_sensitivity(params: dict, contracts, paths, n_steps, seed, trunc=0, scheme=0,
-                                  prec="fp32", draws=DRAWS):
-    """Per-path oracle records (n, 15) and estimators (n, C, 6) on the paths'
-    own normals, and the largest absolute change of each over `draws` runs
-    with every normal moved uniformly within the FP32 (1e-7 + 1.5e-6 R) or the
-    FP64 (1e-15 R) normal-error bound -- and, for FP32, the inputs rounded to
-    FP32.  The change measures how much rounding of the size the GPU path
-    makes can move each per-path quantity: the tangents, which pass through
-    1 / sqrt(V), move most on paths that come near V = 0."""
-    paths = np.asarray(paths, dtype=np.uint64)
-    Za = np.empty((len(paths), n_steps))
-    Zb = np.empty_like(Za)
-    for i, q in enumerate(paths):
-        Za[i], Zb[i] = oracle.path_normals(seed, int(q), n_steps)
+def paths_with_sensitivity(params: dict, contracts, Za, Zb, trunc=0, scheme=0, prec="fp32",
+                           eps_abs=None, eps_rel=None, seed=0, draws=DRAWS):
+    """Oracle records (n, 15) and estimators (n, C, 6) of paths from given
+    normals (n, N), and the largest absolute change of each over `draws` runs
+    with every normal moved uniformly within eps_abs + eps_rel * R (default:
+    the FP32 or FP64 Box-Muller bound) and, for FP32, the inputs rounded to
+    FP32."""
     cs = [oracle.Contract(*c) for c in contracts]
     rec, est = oracle.paths_from_normals(oracle.Params(**params), cs, Za, Zb, trunc, scheme)
     if prec == "fp32":
         P = oracle.Params(**rounded_params(params))
         cs_p = [oracle.Contract(*rounded_contract(c)) for c in contracts]
-        eps_abs, eps_rel = FP32_NORMAL_ABS, FP32_NORMAL_REL
+        ea, er = FP32_NORMAL_ABS, FP32_NORMAL_REL
     else:
         P, cs_p = oracle.Params(**params), cs
-        eps_abs, eps_rel = 0.0, FP64_NORMAL_REL
-    bound = eps_abs + eps_rel * np.hypot(Za, Zb)
+        ea, er = 0.0, FP64_NORMAL_REL
+    ea = ea if eps_abs is None else eps_abs
+    er = er if eps_rel is None else eps_rel
+    bound = ea + er * np.hypot(Za, Zb)
     g = np.random.default_rng(seed ^ 0x5EED)
     drec = np.zeros_like(rec)
     dest = np.zeros_like(est)
@@ -126,6 +121,20 @@ def oracle_paths_with_sensitivity(params: dict, contracts, paths, n_steps, seed,
             drec = np.fmax(drec, np.abs(r - rec))
             dest = np.fmax(dest, np.abs(e - est))
     return rec, est, drec, dest
+
+
+def oracle_paths_with_sensitivity(params: dict, contracts, paths, n_steps, seed, trunc=0, scheme=0,
+                                  prec="fp32", draws=DRAWS):
+    """paths_with_sensitivity on the paths' own Philox normals: the change
+    measures how much rounding of the size the GPU path makes can move each
+    per-path quantity; the tangents, which pass through 1 / sqrt(V), move
+    most on paths that come near V = 0."""
+    paths = np.asarray(paths, dtype=np.uint64)
+    Za = np.empty((len(paths), n_steps))
+    Zb = np.empty_like(Za)
+    for i, q in enumerate(paths):
+        Za[i], Zb[i] = oracle.path_normals(seed, int(q), n_steps)
+    return paths_with_sensitivity(params, contracts, Za, Zb, trunc, scheme, prec, seed=seed, draws=draws)
 
 
 def path_scales(rec_o, est_o, params, contracts, n_steps):
