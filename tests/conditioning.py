@@ -137,6 +137,29 @@ def oracle_paths_with_sensitivity(params: dict, contracts, paths, n_steps, seed,
     return paths_with_sensitivity(params, contracts, Za, Zb, trunc, scheme, prec, seed=seed, draws=draws)
 
 
+# Randomised-QMC normals in FP32: the Brownian bridge forms each W by
+# interpolation from two stored values and each step normal as W_{k+1} - W_k,
+# so the rounding of a step normal scales with the size of the path's W
+# (|W| ~ sqrt(N) in step units), not with the normal's own size.  A time-ordered
+# FP32 bridge stays within 3 * 2^-24 * max_k |W_k| per step normal on the
+# Sobol points (tested against an emulation on the CPU); the bound below takes
+# 4, plus the Box-Muller-sized terms for the inverse normal of each node.
+QMC_BRIDGE_ABS = 4.0 * 2.0 ** -24
+
+
+def qmc_normal_bound(Za, Zb):
+    """Per-path absolute bound (n, 1) on the FP32 error of bridge step normals."""
+    Wmax = np.maximum(np.abs(np.cumsum(Za, axis=1)).max(axis=1), np.abs(np.cumsum(Zb, axis=1)).max(axis=1))
+    return (QMC_BRIDGE_ABS * Wmax + FP32_NORMAL_ABS)[:, None]
+
+
+def qmc_paths_with_sensitivity(params: dict, contracts, Za, Zb, trunc=0, seed=0, draws=DRAWS):
+    """paths_with_sensitivity on QMC bridge normals, with the bridge's FP32
+    error bound (qmc_normal_bound) in place of the Box-Muller one."""
+    return paths_with_sensitivity(params, contracts, Za, Zb, trunc, 0, "fp32",
+                                  qmc_normal_bound(Za, Zb), FP32_NORMAL_REL, seed, draws)
+
+
 def path_scales(rec_o, est_o, params, contracts, n_steps):
     """The scale each per-path quantity is compared relative to: X (= ln S_T/S0)
     max(1, |X|); V max(|V|, theta, v0); dV/dT also at least max(theta, v0) / T
