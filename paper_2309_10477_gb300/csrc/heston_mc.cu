@@ -658,9 +658,10 @@ QmcTables qmc_tables_at(const void *base, const QmcLayout &L)
                      (const BridgeOp *)(b + L.off_ev), (const int32_t *)(b + L.off_evoff)};
 }
 
-// QMC workspace: tile rows | replicate sums | U [tpr][D] | shifts [R][D].
+// QMC workspace: tile rows | group sums [R][gpr] | replicate averages [R][6 nc] |
+// U [tpr][D] | shifts [R][D].
 struct QmcWs {
-    size_t off_rows, off_rep, off_U, off_shift, total;
+    size_t off_rows, off_groups, off_rep, off_U, off_shift, total;
 };
 
 QmcWs qmc_ws_layout(uint32_t nc, uint64_t n_paths, uint32_t N, uint32_t R)
@@ -671,8 +672,9 @@ QmcWs qmc_ws_layout(uint32_t nc, uint64_t n_paths, uint32_t N, uint32_t R)
     const size_t D = 2u * (size_t)N;
     QmcWs L;
     L.off_rows = 0;
-    L.off_rep = align256(tiles * w);
-    L.off_U = L.off_rep + align256((size_t)R * w);
+    L.off_groups = align256(tiles * w);
+    L.off_rep = L.off_groups + align256((size_t)R * groups_for(tpr) * w);
+    L.off_U = L.off_rep + align256((size_t)R * 6u * nc * sizeof(double));
     L.off_shift = L.off_U + align256(tpr * D * sizeof(uint32_t));
     L.total = L.off_shift + align256((size_t)R * D * sizeof(uint32_t));
     return L;
@@ -753,11 +755,15 @@ int enqueue_qmc(const Prepared &pp, uint64_t n_paths, uint64_t seed, const void 
                 : mon == MON_EVERY ? launch_qmc_t<1, MON_EVERY>(pp, a, st) : launch_qmc_t<1, MON_STRIDE>(pp, a, st);
     if (e != cudaSuccess) return HESTON_ERR_CUDA;
     const int width = 12 * pp.cs.n;
-    double *rep = (double *)(b + WL.off_rep);
-    reduce_replicates_kernel<<<R, 128, 0, st>>>(a.tile_sums, a.tpr, width, rep);
+    const uint32_t gpr = (uint32_t)groups_for(a.tpr);
+    double *groups = (double *)(b + WL.off_groups);
+    // one thread per (column, part) pair of the fixed-order sums, as launch_reduce
+    const int threads = std::min(1024, ((8 * width + 31) / 32) * 32);
+    reduce_replicate_groups_kernel<<<(unsigned)((uint64_t)R * gpr), threads, 0, st>>>(a.tile_sums, a.tpr, gpr,
+                                                                                      width, groups);
     if (cudaGetLastError() != cudaSuccess) return HESTON_ERR_CUDA;
-    reduce_final_qmc_kernel<<<1, 128, 0, st>>>(rep, R, pp.cs.n, (double)(n_paths / R),
-                                               pp.gamma_nan ? 1 : 0, d_out);
+    reduce_final_qmc_kernel<<<1, 256, 0, st>>>(groups, R, gpr, pp.cs.n, (double)(n_paths / R),
+                                               pp.gamma_nan ? 1 : 0, (double *)(b + WL.off_rep), d_out);
     return cudaGetLastError() == cudaSuccess ? HESTON_OK : HESTON_ERR_CUDA;
 }
 
@@ -773,13 +779,14 @@ int build_qmc_tables(uint32_t N, void *d_tables, size_t bytes)
     uint32_t *V = (uint32_t *)(h.data() + L.off_V);
     uint32_t *T = (uint32_t *)(h.data() + L.off_T);
     sobol_directions_host(D, V);
-    // interleaved per bridge node j and lane l: x_{2j}(l), x_{2j}(l + 32), x_{2j+1}(l), x_{2j+1}(l + 32)
+    // interleaved per bridge node j and lane l: x_{2j}(l), x_{2j}(l + 32), x_{2j+1}(l), x_{2j+1}(l + 32),
+    // low 8 bits cleared (the uniform uses the top 24 bits of a word)
     for (uint32_t d = 0; d < D; ++d)
         for (uint32_t p = 0; p < 64; ++p) {
             uint32_t x = 0;
             for (int b = 0; b < 6; ++b)
                 if ((p >> b) & 1u) x ^= V[d * 32u + b];
-            T[((d >> 1) * 32u + (p & 31u)) * 4u + (d & 1u) * 2u + (p >> 5)] = x;
+            T[((d >> 1) * 32u + (p & 31u)) * 4u + (d & 1u) * 2u + (p >> 5)] = x & 0xFFFFFF00u;
         }
     std::memcpy(h.data() + L.off_evoff, plan.off.data(), plan.off.size() * sizeof(int32_t));
     std::memcpy(h.data() + L.off_ev, plan.ev.data(), plan.ev.size() * sizeof(BridgeOp));
