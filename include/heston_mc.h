@@ -515,6 +515,15 @@ int heston_mc_debug_paths(const heston_params *params, const heston_contract *co
 int heston_rng_debug(uint64_t rng_seed, const uint64_t *paths, const uint32_t *steps,
                      uint32_t count, int32_t prec, uint32_t *h_words, double *h_normals);
 
+/* The FP64 Box-Muller's table-driven logarithm and sine/cosine beside
+ * CUDA's, for tests (Sec. 2.4's normals; the uniforms are those of the
+ * random-number contract above): for i in [0, count), with n = first + i + 1
+ * and g = first + i, h_out (host, count x 6 doubles) receives ln(n 2^-24) by
+ * the table method and by CUDA's log, then sin and cos of 2 pi g 2^-24 by
+ * the table method and by CUDA's sincospi.  first + count <= 2^24, count >= 1
+ * (HESTON_ERR_INVALID_ARG otherwise).  Synchronous; allocates device memory. */
+int heston_bm64_debug(uint32_t first, uint32_t count, double *h_out);
+
 /* Static description of a status code (never NULL). */
 const char *heston_status_string(int status);
 

@@ -1671,6 +1671,23 @@ int heston_rng_debug(uint64_t rng_seed, const uint64_t *paths, const uint32_t *s
     return e;
 }
 
+int heston_bm64_debug(uint32_t first, uint32_t count, double *h_out)
+{
+    if (!h_out || count == 0 || (uint64_t)first + count > (1ull << 24)) return HESTON_ERR_INVALID_ARG;
+    const size_t bytes = 6 * sizeof(double) * (size_t)count;
+    double *d = nullptr;
+    if (cudaMalloc((void **)&d, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return HESTON_ERR_NOMEM;
+    }
+    int e = HESTON_OK;
+    bm64_debug_kernel<<<(count + 255) / 256, 256>>>(first, count, d);
+    if (cudaGetLastError() != cudaSuccess || cudaMemcpy(h_out, d, bytes, cudaMemcpyDeviceToHost) != cudaSuccess)
+        e = HESTON_ERR_CUDA;
+    cudaFree(d);
+    return e;
+}
+
 int heston_batch_plan_make(const heston_batch_item *items, uint32_t n_items,
                            const heston_options *opts, heston_batch_plan *plan)
 {

@@ -129,6 +129,7 @@ def load():
                                    P(heston_options), P(u64), u32, P(ctypes.c_double),
                                    P(ctypes.c_double)], i32),
         "heston_rng_debug": ([u64, P(u64), P(u32), u32, i32, P(u32), P(ctypes.c_double)], i32),
+        "heston_bm64_debug": ([u32, u32, P(ctypes.c_double)], i32),
         "heston_status_string": ([ctypes.c_int], ctypes.c_char_p),
         "heston_batch_plan_make": ([P(heston_batch_item), u32, P(heston_options),
                                     P(heston_batch_plan)], i32),
@@ -299,6 +300,15 @@ def heston_rng_debug(rng_seed, paths, steps, prec=HESTON_FP64):
                                    words.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
                                    normals.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
     return words, normals
+
+
+def heston_bm64_debug(first: int, count: int) -> np.ndarray:
+    """(count, 6): ln(n 2^-24) by the FP64 Box-Muller's table method and by
+    CUDA's log (n = first + i + 1), then sin and cos of 2 pi g 2^-24 by the
+    table method and by CUDA's sincospi (g = first + i)."""
+    out = np.zeros((count, 6))
+    _check(load().heston_bm64_debug(first, count, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return out
 
 
 def results_to_arrays(results):
