@@ -67,6 +67,12 @@ FP64_OPS_PER_PATH_STEP = 47
 # SM sub-partition.
 HEAVY_CYCLES_PER_LANE_STEP = 176
 HEAVY_LANE_STEP_PATHS = 64
+# The same mix measured: the heavy_mix micro-benchmark runs one lane's heavy-pipe
+# work per step (20 wide multiplies + 48 f32x2 FMAs = 68 instructions, two
+# path-steps) on independent chains; its rate / 68 x 2 is the path-steps/s
+# ceiling of that mix on this GPU.
+MIX_INSTS_PER_UNIT = 68
+MIX_PATH_STEPS_PER_UNIT = 2
 FLUSH_BYTES = 256 << 20               # > 129 MB L2
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "heston_paths_kernel_multi_strike_2p22.md")
 KERNEL_SOURCE = os.path.join(ROOT, "paper_2309_10477_gb300", "csrc", "heston_device.cuh")
@@ -869,12 +875,14 @@ def run_gpu(args):
         nominal_tinst = n_sm * ISSUE_LANES_PER_SM_CLK * max_mhz * 1e6 / 1e12
         # measured: the FP32 FMA rate, one thread-instruction per lane per clock, the
         # highest rate any instruction kind reaches (the machine's issue rate)
-        peak_tinst = (max(v["thread_insts_per_s"] for v in pk.values()) / 1e12 if pk
+        peak_tinst = (max(v["thread_insts_per_s"] for k_, v in pk.items() if k_ != "heavy_mix") / 1e12 if pk
                       else nominal_tinst)
         achieved_tinst = path_steps * ALGO_SLOTS_PER_PATH_STEP / (k1 * 1e-3) / 1e12
         pk_clk = clocks.summary_between(*t_pk)
         pk_mhz = pk_clk.get("sm_mhz") or max_mhz
         traffic = _profiled_traffic()
+        mix_ceiling = (None if not pk or "heavy_mix" not in pk else
+                       pk["heavy_mix"]["thread_insts_per_s"] / MIX_INSTS_PER_UNIT * MIX_PATH_STEPS_PER_UNIT)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
@@ -920,7 +928,12 @@ def run_gpu(args):
                              * (pk_mhz or max_mhz) * 1e6 / HEAVY_CYCLES_PER_LANE_STEP,
                              "frac": (path_steps / (k1 * 1e-3)) / (HEAVY_LANE_STEP_PATHS * 4 * n_sm
                                                                   * (pk_mhz or max_mhz) * 1e6
-                                                                  / HEAVY_CYCLES_PER_LANE_STEP)},
+                                                                  / HEAVY_CYCLES_PER_LANE_STEP),
+                             "ceiling_measured_path_steps_per_s": mix_ceiling,
+                             "frac_measured": (None if mix_ceiling is None
+                                               else (path_steps / (k1 * 1e-3)) / mix_ceiling),
+                             "measured_by": "heavy_mix micro-benchmark (20 wide multiplies + 48 f32x2 "
+                                            "FMAs per lane and step, independent chains, this run)"},
                          "kernel_ms": k1,
                          "path_steps_per_s_kernel": path_steps / (k1 * 1e-3)},
             "pipe_peaks": None if pk is None else {

@@ -1,8 +1,11 @@
 // pipe_peaks.cu -- issue-rate micro-benchmarks that give the roofline
 // denominators of the path kernels, measured on the GPU that runs them:
 // FP32 FMA (scalar and the f32x2 packed form), the 32x32->64 wide integer
-// multiply and the three-way xor of Philox4x32-10, the special-function unit
-// (ex2, lg2, sin, cos, rsqrt, sqrt approximations) and FP64 FMA.
+// multiply (and its low and high 32-bit halves alone) and the three-way xor
+// of Philox4x32-10, the special-function unit (ex2, lg2, sin, cos, rsqrt,
+// sqrt approximations), FP64 FMA, and the FMA-pipe mix of the packed path
+// kernel: 20 wide multiplies per 48 f32x2 FMAs, the heavy-pipe work of one
+// lane's two paths over one step.
 //
 // Each thread runs kChains independent dependency chains of one instruction
 // kind in an unrolled loop, so that with enough resident warps the pipe, not
@@ -24,8 +27,10 @@ constexpr int kUnroll = 8;       // chain steps per loop iteration
 
 enum Kind {
     K_FFMA = 0, K_FFMA2 = 1, K_IMAD_WIDE = 2, K_LOP3 = 3, K_EX2 = 4, K_LG2 = 5, K_SIN = 6,
-    K_COS = 7, K_RSQRT = 8, K_SQRT = 9, K_DFMA = 10, K_COUNT = 11
+    K_COS = 7, K_RSQRT = 8, K_SQRT = 9, K_DFMA = 10, K_IMAD_LO = 11, K_IMAD_HI = 12, K_MIX = 13,
+    K_COUNT = 14
 };
+constexpr int kMixInstsPerUnit = 68;     // 20 wide multiplies + 48 f32x2 FMAs
 
 __device__ __forceinline__ float mufu(int kind, float x)
 {
@@ -124,6 +129,57 @@ __global__ void peak_kernel(uint32_t iters, float fa, float fb, float *sink)
 #pragma unroll
         for (int i = 0; i < kChains; ++i) s += x[i];
         if (s == 12345u) sink[0] = (float)s;
+    } else if constexpr (KIND == K_IMAD_LO || KIND == K_IMAD_HI) {
+        // x = lo(x m) + c, or x = hi(x m) + c: each half of the wide multiply alone
+        uint32_t x[kChains];
+        const uint32_t m = 0xCD9E8D57u ^ __float_as_uint(fa), c = 0x9E3779B9u ^ __float_as_uint(fb);
+#pragma unroll
+        for (int i = 0; i < kChains; ++i) x[i] = tid * 747796405u + (uint32_t)i;
+        for (uint32_t it = 0; it < iters; ++it) {
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+#pragma unroll
+                for (int i = 0; i < kChains; ++i) {
+                    if constexpr (KIND == K_IMAD_LO)
+                        asm volatile("mad.lo.u32 %0, %1, %2, %3;" : "=r"(x[i]) : "r"(x[i]), "r"(m), "r"(c));
+                    else
+                        asm volatile("mad.hi.u32 %0, %1, %2, %3;" : "=r"(x[i]) : "r"(x[i]), "r"(m), "r"(c));
+                }
+            }
+        }
+        uint32_t s = 0;
+#pragma unroll
+        for (int i = 0; i < kChains; ++i) s += x[i];
+        if (s == 12345u) sink[0] = (float)s;
+    } else if constexpr (KIND == K_MIX) {
+        // per unrolled step 5 wide multiplies and 12 f32x2 FMAs on independent
+        // chains: a quarter of one mix unit (20 : 48)
+        unsigned long long d[5];
+        float2 x[12];
+        const uint32_t m = 0xD2511F53u ^ (uint32_t)__float_as_uint(fa);
+        const float2 a = make_float2(fa, fa), b = make_float2(fb, fb);
+#pragma unroll
+        for (int i = 0; i < 5; ++i) d[i] = tid * 2654435761ull + (unsigned long long)i;
+#pragma unroll
+        for (int i = 0; i < 12; ++i) x[i] = make_float2(1.0f + 1e-3f * (float)(tid + i), 1.0f);
+        for (uint32_t it = 0; it < iters; ++it) {
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+#pragma unroll
+                for (int i = 0; i < 12; ++i) {
+                    x[i] = __ffma2_rn(x[i], a, b);
+                    if (i < 5)
+                        asm volatile("mad.wide.u32 %0, %1, %2, %3;" : "=l"(d[i]) : "r"((uint32_t)d[i]), "r"(m), "l"(d[i]));
+                }
+            }
+        }
+        unsigned long long s = 0;
+        float f = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 5; ++i) s ^= d[i];
+#pragma unroll
+        for (int i = 0; i < 12; ++i) f += x[i].x + x[i].y;
+        if (s == 12345ull || f == 1234.5f) sink[0] = f + (float)s;
     } else if constexpr (KIND == K_DFMA) {
         double x[kChains];
         const double a = (double)fa, b = (double)fb;
@@ -178,14 +234,16 @@ int pipe_peak_kinds(void) { return K_COUNT; }
 const char *pipe_peak_name(int kind)
 {
     static const char *names[K_COUNT] = {"ffma", "ffma2", "imad_wide", "lop3", "mufu_ex2", "mufu_lg2",
-                                         "mufu_sin", "mufu_cos", "mufu_rsqrt", "mufu_sqrt", "dfma"};
+                                         "mufu_sin", "mufu_cos", "mufu_rsqrt", "mufu_sqrt", "dfma",
+                                         "imad_lo", "imad_hi", "heavy_mix"};
     return (kind >= 0 && kind < K_COUNT) ? names[kind] : "";
 }
 
 // Enqueue one launch of kind `kind` on `stream` (cudaStream_t or NULL) with
 // `blocks` x `threads` threads and `iters` loop iterations; d_sink is a device
 // float that the kernel writes only in a case that never happens.  Writes
-// the executed thread-instructions of the measured kind to *thread_insts.
+// the executed thread-instructions of the measured kind to *thread_insts (for
+// the mix, 68 per unit of 20 wide multiplies and 48 f32x2 FMAs).
 // Returns 0, or -1 for bad arguments, -2 for a launch error.
 int pipe_peak_launch(int kind, uint32_t blocks, uint32_t threads, uint32_t iters, void *stream,
                      float *d_sink, double *thread_insts)
@@ -206,10 +264,15 @@ int pipe_peak_launch(int kind, uint32_t blocks, uint32_t threads, uint32_t iters
     case K_COS: e = launch_kind<K_COS>(blocks, threads, iters, st, d_sink); break;
     case K_RSQRT: e = launch_kind<K_RSQRT>(blocks, threads, iters, st, d_sink); break;
     case K_SQRT: e = launch_kind<K_SQRT>(blocks, threads, iters, st, d_sink); break;
-    default: e = launch_kind<K_DFMA>(blocks, threads, iters, st, d_sink); break;
+    case K_DFMA: e = launch_kind<K_DFMA>(blocks, threads, iters, st, d_sink); break;
+    case K_IMAD_LO: e = launch_kind<K_IMAD_LO>(blocks, threads, iters, st, d_sink); break;
+    case K_IMAD_HI: e = launch_kind<K_IMAD_HI>(blocks, threads, iters, st, d_sink); break;
+    default: e = launch_kind<K_MIX>(blocks, threads, iters, st, d_sink); break;
     }
     if (e != cudaSuccess) return -2;
-    *thread_insts = (double)blocks * threads * (double)iters * kUnroll * kChains;
+    // the mix: kUnroll quarter-units per iteration, kMixInstsPerUnit instructions per unit
+    *thread_insts = kind == K_MIX ? (double)blocks * threads * (double)iters * kUnroll / 4.0 * kMixInstsPerUnit
+                                  : (double)blocks * threads * (double)iters * kUnroll * kChains;
     return 0;
 }
 
