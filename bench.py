@@ -337,6 +337,15 @@ def cpu_baseline(target_s: float = 10.0):
                       f"oracle on {threads} host threads ({dt:.1f} s)"}
 
 
+def _workload_config(w, n, nc):
+    """The workload's description, the same in both arms (what is computed, not
+    how): the configuration is named by what it is, with its sizes."""
+    return {"workload": w.name if n == w.n_paths else f"{w.name} (n_paths={n})",
+            "n_paths": n, "n_steps": w.n_steps,
+            "contracts": "European + Asian(M=252) calls, K in {90,100,110}",
+            "estimates": 6 * nc, "truncation": "full", "rng": "philox4x32-10"}
+
+
 def run_reference(args):
     rank, world, _ = _dist_env()
     if rank != 0:
@@ -356,8 +365,10 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": w.name, "n_paths_per_step": n, "n_steps": w.n_steps,
-                   "contracts": 6, "sample": f"{n} of {w.n_paths} paths per step"},
+        "config": _workload_config(w, w.n_paths, len(cs)),
+        "sample": f"{n} of {w.n_paths} paths per timed step (value = sampled path-steps / time)",
+        "precision": "fp64 oracle path and sums",
+        "parallelism": f"{threads} host threads (OpenMP over fixed path chunks)",
         "greek_sets_per_s": 6.0 / step_s,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": f"{n} paths x {w.n_steps} steps per step, FP64 oracle"},
@@ -888,12 +899,9 @@ def run_gpu(args):
             "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": w.name if n == w.n_paths else f"{w.name} (n_paths={n})",
-                       "n_paths": n, "n_steps": w.n_steps,
-                       "contracts": "European + Asian(M=252) calls, K in {90,100,110}",
-                       "estimates": 6 * nc, "truncation": "full", "rng": "philox4x32-10",
-                       "precision": "fp32 path, fp64 sums", "parallelism": f"dp{world} (path ranges)",
-                       "l2": "flushed between timed steps (256 MiB write outside the events)"},
+            "config": _workload_config(w, n, nc),
+            "precision": "fp32 path, fp64 sums", "parallelism": f"dp{world} (path ranges)",
+            "l2": "flushed between timed steps (256 MiB write outside the events)",
             "greek_sets_per_s": world * nc / (ms * 1e-3),
             "price_se_k100_euro": float(estimates[1, 6]),
             "fixed_se_note": "SE target = the FP64 oracle's SE on the same normals; the GPU SE "
