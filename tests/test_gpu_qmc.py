@@ -65,8 +65,10 @@ def test_qmc_per_path(nv, pset, N, trunc):
 
 
 # N = 2048 is the largest step count; its bridge plan and Sobol rows need more
-# than 48 KB of shared memory per block, which the launch opts in to
-@pytest.mark.parametrize("N,P,R", [(50, 4096, 8), (252, 1024, 4), (2048, 64, 8)])
+# than 48 KB of shared memory per block, which the launch opts in to.  (252,
+# 2^17, 2): the bench's points per replicate and steps -- each replicate's tiles
+# are those of the bench's 32-replicate launch, whatever the replicate count.
+@pytest.mark.parametrize("N,P,R", [(50, 4096, 8), (252, 1024, 4), (2048, 64, 8), (252, 1 << 17, 2)])
 def test_qmc_estimates_match_oracle(nv, N, P, R):
     cs = [(0, 90.0, 1.0, 0, 0), (0, 110.0, 1.0, 0, 0), (1, 100.0, 1.0, 0, 0), (1, 100.0, 1.0, 1, 0)]
     opts = nv.make_options(prec=nv.HESTON_FP32, rng=nv.HESTON_RNG_SOBOL_BB, n_shifts=R)
