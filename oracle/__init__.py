@@ -74,39 +74,64 @@ class _Contract(ctypes.Structure):
 def _load():
     global _lib
     if _lib is None:
-        lib = ctypes.CDLL(build())
-        P = ctypes.POINTER
-        d, u32, u64, i32 = ctypes.c_double, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
-        lib.orc_philox4x32_10.argtypes = [P(u32), P(u32), P(u32)]
-        lib.orc_uniform_pair.argtypes = [u64, u64, u32, u32, P(d), P(d)]
-        lib.orc_normal_pair.argtypes = [u64, u64, u32, u32, P(d), P(d)]
-        lib.orc_path_normals.argtypes = [u64, u64, u32, u32, P(d), P(d)]
-        lib.orc_mc_sums.argtypes = [P(_Params), P(_Contract), u32, u64, u64, u32, u64, i32, i32,
-                                    i32, P(d), P(d)]
-        lib.orc_mc_sums.restype = i32
-        lib.orc_mc_sums_perturbed.argtypes = [P(_Params), P(_Contract), u32, u64, u64, u32, u64, i32,
-                                              i32, i32, d, d, u64, P(d), P(d)]
-        lib.orc_mc_sums_perturbed.restype = i32
-        lib.orc_debug_paths.argtypes = [P(_Params), P(_Contract), u32, P(u64), u64, u32, u64, i32,
-                                        i32, P(d), P(d)]
-        lib.orc_debug_paths.restype = i32
-        lib.orc_path_from_normals.argtypes = [P(_Params), P(_Contract), u32, u32, i32, i32, P(d), P(d),
-                                              P(d), P(d), P(d), P(d)]
-        lib.orc_path_from_normals.restype = i32
-        lib.orc_paths_from_normals.argtypes = [P(_Params), P(_Contract), u32, u32, i32, i32, u64,
-                                               P(d), P(d), P(d), P(d)]
-        lib.orc_paths_from_normals.restype = i32
-        lib.orc_mc_gradient.argtypes = [P(_Params), P(_Contract), u64, u32, u64, P(d), P(d)]
-        lib.orc_mc_gradient.restype = i32
-        lib.orc_debug_gradients.argtypes = [P(_Params), P(_Contract), P(u64), u64, u32, u64, P(d)]
-        lib.orc_debug_gradients.restype = i32
-        lib.orc_gradients_from_normals.argtypes = [P(_Params), P(_Contract), u32, u64, P(d), P(d), P(d)]
-        lib.orc_gradients_from_normals.restype = i32
-        lib.orc_max_threads.restype = i32
-        lib.orc_set_threads.argtypes = [i32]
-        lib.orc_set_threads.restype = None
-        _lib = lib
+        _lib = _configure(ctypes.CDLL(build()))
     return _lib
+
+
+def _configure(lib):
+    """Declare the argument and return types of the library's entry points."""
+    P = ctypes.POINTER
+    d, u32, u64, i32 = ctypes.c_double, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+    lib.orc_philox4x32_10.argtypes = [P(u32), P(u32), P(u32)]
+    lib.orc_uniform_pair.argtypes = [u64, u64, u32, u32, P(d), P(d)]
+    lib.orc_normal_pair.argtypes = [u64, u64, u32, u32, P(d), P(d)]
+    lib.orc_path_normals.argtypes = [u64, u64, u32, u32, P(d), P(d)]
+    lib.orc_mc_sums.argtypes = [P(_Params), P(_Contract), u32, u64, u64, u32, u64, i32, i32,
+                                i32, P(d), P(d)]
+    lib.orc_mc_sums.restype = i32
+    lib.orc_mc_sums_perturbed.argtypes = [P(_Params), P(_Contract), u32, u64, u64, u32, u64, i32,
+                                          i32, i32, d, d, u64, P(d), P(d)]
+    lib.orc_mc_sums_perturbed.restype = i32
+    lib.orc_debug_paths.argtypes = [P(_Params), P(_Contract), u32, P(u64), u64, u32, u64, i32,
+                                    i32, P(d), P(d)]
+    lib.orc_debug_paths.restype = i32
+    lib.orc_path_from_normals.argtypes = [P(_Params), P(_Contract), u32, u32, i32, i32, P(d), P(d),
+                                          P(d), P(d), P(d), P(d)]
+    lib.orc_path_from_normals.restype = i32
+    lib.orc_paths_from_normals.argtypes = [P(_Params), P(_Contract), u32, u32, i32, i32, u64,
+                                           P(d), P(d), P(d), P(d)]
+    lib.orc_paths_from_normals.restype = i32
+    lib.orc_mc_gradient.argtypes = [P(_Params), P(_Contract), u64, u32, u64, P(d), P(d)]
+    lib.orc_mc_gradient.restype = i32
+    lib.orc_debug_gradients.argtypes = [P(_Params), P(_Contract), P(u64), u64, u32, u64, P(d)]
+    lib.orc_debug_gradients.restype = i32
+    lib.orc_gradients_from_normals.argtypes = [P(_Params), P(_Contract), u32, u64, P(d), P(d), P(d)]
+    lib.orc_gradients_from_normals.restype = i32
+    lib.orc_max_threads.restype = i32
+    lib.orc_set_threads.argtypes = [i32]
+    lib.orc_set_threads.restype = None
+    return lib
+
+
+class using_library:
+    """Test support: route every oracle call through another build of
+    heston_oracle.c (a copy with a mistake planted in it) for the duration of
+    a ``with`` block, then restore the library in use before."""
+
+    def __init__(self, path: str):
+        self.path = path
+        self.saved = None
+
+    def __enter__(self):
+        global _lib
+        self.saved = _lib
+        _lib = _configure(ctypes.CDLL(self.path))
+        return _lib
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self.saved
+        return False
 
 
 def _dptr(a):

@@ -207,25 +207,29 @@ def test_picked_normals_through_both_branches(name, floor):
         assert went_negative >= 1          # the truncation branch was exercised
 
 
+@pytest.mark.parametrize("begin", [0, 2**32 - 2])
 @pytest.mark.parametrize("n_paths", [1, 2, 3])
 @pytest.mark.parametrize("N", [1, 2])
-def test_monte_carlo_sums_mean_and_se_by_hand(n_paths, N):
+def test_monte_carlo_sums_mean_and_se_by_hand(n_paths, N, begin):
     """Alg. "Monte Carlo option pricing estimation": sum over the paths, then
-    mean = sum / n and SE = sqrt((sum x^2 - n mean^2) / (n - 1) / n)."""
+    mean = sum / n and SE = sqrt((sum x^2 - n mean^2) / (n - 1) / n).  A range
+    of paths [begin, begin + n) sums the paths of those global indices (the
+    contract a path-range shard relies on), here across the low counter
+    word's wrap at 2^32."""
     p = PARAMS["paper"]
     seed = 77
     cs = CONTRACTS[:4]
     est = []
-    for path in range(n_paths):
+    for path in range(begin, begin + n_paths):
         Za, Zb = oracle.path_normals(seed, path, N)
         rec = record_by_hand(p, 1.0, N, N, Za, Zb, 0)
         est.append([estimators_by_hand(p, c, N, rec) for c in cs])
     est = np.array(est)                              # (n, C, 6)
     s_h = est.sum(axis=0)
     s2_h = (est * est).sum(axis=0)
-    s_o, s2_o = oracle.mc_sums(oracle.Params(**p), _oc(cs), n_paths, N, seed)
+    s_o, s2_o = oracle.mc_sums(oracle.Params(**p), _oc(cs), n_paths, N, seed, path_begin=begin)
     assert _close(s_o, s_h) and _close(s2_o, s2_h)
-    if n_paths >= 2:
+    if n_paths >= 2 and begin == 0:
         mean_h = s_h / n_paths
         se_h = np.sqrt(np.maximum((s2_h - n_paths * mean_h * mean_h) / (n_paths - 1), 0.0) / n_paths)
         mean_o, se_o = oracle.mc_price_greeks(oracle.Params(**p), _oc(cs), n_paths, N, seed)
