@@ -3,7 +3,8 @@ mistake in a copy of oracle/heston_oracle.c (a dropped term, a wrong sign,
 index or operand, a wrong constant, the paper's printed Asian Rho), builds it,
 routes the oracle through that build, and runs the oracle's own pin tests
 (brute force by hand, the RNG against cuRAND's host generator, the two-date
-Asian integral, the schemes' closed forms, moments and finite differences)
+Asian integral, the parameter gradient against finite differences and the
+closed form, the schemes' closed forms, moments and finite differences)
 until one fails.
 Every mistake must fail at least one pin; the unchanged copy must pass all
 of them."""
@@ -97,6 +98,15 @@ MUTATIONS = [
      "const double ut = sqrt(dt * (V + Vn));"),
     ("QE v0-tangent without the factor 2", "*Vn_v = a_v * (b + Za) * (b + Za) + 2.0 * a * (b + Za) * b_v;",
      "*Vn_v = a_v * (b + Za) * (b + Za) + a * (b + Za) * b_v;"),
+    # the forward-mode parameter gradient (the adjoint kernel's reference)
+    ("gradient dZ2/drho sign", "const double dZ2 = (i == 5) ? za - (p->rho / sq) * zb : 0.0;",
+     "const double dZ2 = (i == 5) ? za + (p->rho / sq) * zb : 0.0;"),
+    ("gradient drift without r", "nX[i] = dX[i] + dr * dt - 0.5 * dVp * dt + du * za;",
+     "nX[i] = dX[i] - 0.5 * dVp * dt + du * za;"),
+    ("gradient Milstein xi-term halved", "+ (0.5 * p->xi * dxi * dt * (Z2 * Z2 - 1.0)",
+     "+ (0.25 * p->xi * dxi * dt * (Z2 * Z2 - 1.0)"),
+    ("gradient without the discount derivative", "grad[6] += -T * D * phi;", "grad[6] += 0.0 * T * D * phi;"),
+    ("gradient S0 scaling missing", "dAval[0] += Aval / p->S0;", "dAval[0] += 0.0;"),
     # Monte Carlo sums
     ("sum of squares without the square", "s[E + c * 6 + e] += est[e] * est[e];", "s[E + c * 6 + e] += est[e];"),
     ("path index without its range start", "orc_path_normals(seed, path_begin + i, N, 0u, Za, Zb);",
@@ -105,7 +115,7 @@ MUTATIONS = [
 
 # The pin tests run against each mutant, fastest first.
 PIN_MODULES = ["test_oracle_brute_force", "test_oracle_rng", "test_oracle_asian_two_dates",
-               "test_oracle_schemes", "test_oracle_scheme"]
+               "test_oracle_gradient", "test_oracle_schemes", "test_oracle_scheme"]
 
 
 def _cases(fn):
