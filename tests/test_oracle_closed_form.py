@@ -61,10 +61,11 @@ def test_heston_characteristic_function_matches_quadrature_of_the_pde_free_momen
     assert 0.03 < var < 0.05
 
 
-def test_black_scholes_greeks_are_derivatives_of_price():
+@pytest.mark.parametrize("is_put", [False, True])
+def test_black_scholes_greeks_are_derivatives_of_price(is_put):
     S0, K, T, r, s2 = 100.0, 97.0, 0.9, 0.03, 0.06
-    f = lambda S=S0, t=T, rr=r, v=s2: cf.bs_total_variance(S, K, t, rr, v * t)["price"]
-    g = cf.bs_total_variance(S0, K, T, r, s2 * T, dw_dv0=T, dw_dT=s2)
+    f = lambda S=S0, t=T, rr=r, v=s2: cf.bs_total_variance(S, K, t, rr, v * t, is_put=is_put)["price"]
+    g = cf.bs_total_variance(S0, K, T, r, s2 * T, dw_dv0=T, dw_dT=s2, is_put=is_put)
     h = 1e-5
     assert g["delta"] == pytest.approx((f(S=S0 + h) - f(S=S0 - h)) / (2 * h), rel=1e-6)
     assert g["gamma"] == pytest.approx((f(S=S0 + 1e-3) - 2 * f() + f(S=S0 - 1e-3)) / 1e-6,
@@ -75,6 +76,7 @@ def test_black_scholes_greeks_are_derivatives_of_price():
     # and the price is the discounted lognormal expectation
     sd = math.sqrt(s2 * T)
     mu = math.log(S0) + (r - 0.5 * s2) * T
-    ev, _ = integrate.quad(lambda x: max(math.exp(x) - K, 0.0) * stats.norm.pdf(x, mu, sd),
+    payoff = (lambda x: max(K - math.exp(x), 0.0)) if is_put else (lambda x: max(math.exp(x) - K, 0.0))
+    ev, _ = integrate.quad(lambda x: payoff(x) * stats.norm.pdf(x, mu, sd),
                            mu - 12 * sd, mu + 12 * sd, limit=200)
     assert f() == pytest.approx(math.exp(-r * T) * ev, rel=1e-9)
