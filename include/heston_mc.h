@@ -35,8 +35,13 @@
  * index `path` and time step `step`; words 0-1 feed even steps and words
  * 2-3 odd steps as (u1, u2) with u1 = ((w >> 8) + 1) * 2^-24 and
  * u2 = (w >> 8) * 2^-24; Box-Muller Za = sqrt(-2 ln u1) cos(2 pi u2),
- * Zb = sqrt(-2 ln u1) sin(2 pi u2).  Results are therefore a function of
- * (inputs, seed) only, independent of launch shape, device and sharding.
+ * Zb = sqrt(-2 ln u1) sin(2 pi u2).  The FP32 path evaluates ln, sqrt, sin
+ * and cos with the special-function unit's approximations (its normals lie
+ * within 1e-7 + 1.5e-6 R of the exact ones, R = sqrt(Za^2 + Zb^2)); the FP64
+ * path takes ln u1 and sin/cos(2 pi u2) from table-driven FP64 functions
+ * (within about 2 ulp; see heston_bm64_debug).  Results are therefore a
+ * function of (inputs, seed) only, independent of launch shape, device and
+ * sharding.
  */
 #ifndef HESTON_MC_H
 #define HESTON_MC_H
