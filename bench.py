@@ -593,8 +593,12 @@ def run_gpu(args):
     schemes = None
     if not args.no_schemes and world == 1:
         schemes = {}
-        for sname, sid in (("euler", nv.HESTON_SCHEME_EULER), ("qe", nv.HESTON_SCHEME_QE)):
-            sopts = nv.make_options(prec=nv.HESTON_FP32, stream=stream, device=local, scheme=sid)
+        # the paper's scheme as printed (Milstein, V floored at zero after each
+        # update), Euler, and Andersen's QE, on the same workload and normals
+        for sname, sid, strunc in (("milstein_paper_floor", nv.HESTON_SCHEME_MILSTEIN, nv.HESTON_TRUNC_PAPER_FLOOR),
+                                   ("euler", nv.HESTON_SCHEME_EULER, nv.HESTON_TRUNC_FULL),
+                                   ("qe", nv.HESTON_SCHEME_QE, nv.HESTON_TRUNC_FULL)):
+            sopts = nv.make_options(prec=nv.HESTON_FP32, stream=stream, device=local, scheme=sid, trunc=strunc)
             sout = torch.empty(nc * 12, dtype=torch.float64, device=dev)
 
             def sstep():
