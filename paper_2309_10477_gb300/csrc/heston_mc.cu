@@ -299,14 +299,14 @@ cudaError_t launch_paths_t(const Prepared &pp, const Coef<R> &k, const Launch &a
     int n_sm = 0;
     e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    // FP32 full-truncation Milstein / Euler launches of fewer than 3 tiles per
+    // FP32 launches (every scheme and truncation) of fewer than 3 tiles per
     // SM take the split kernel (two warps per tile, one path per lane): there
     // each packed warp's chain of dependent instructions sets the time, and
     // twice the warps with shorter chains win (2^14 paths: 0.068 -> 0.057 ms);
     // from about 6 tiles per SM the packed kernel's fewer instructions win
     // (2^16: 0.089 ms against 0.100).  An explicit launch shape keeps the
     // packed kernel.
-    if constexpr (split_gamma<R, STEP>()) {
+    if constexpr (packed_f32<R, STEP>()) {
         if (!pp.opt.block_threads && !pp.opt.grid_ctas && a.n_tiles < 3u * (uint64_t)n_sm) {
             int per_sm_split = 0;
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_split, heston_paths_split_kernel<STEP, MON>,

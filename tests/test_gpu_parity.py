@@ -482,12 +482,14 @@ def test_eight_contracts_the_widest_tile_row(nv):
     assert e.value.status == nv.HESTON_ERR_INVALID_ARG
 
 
-@pytest.mark.parametrize("scheme", [0, 1])
+@pytest.mark.parametrize("scheme,trunc", [(0, 0), (1, 0), (0, 1), (1, 1), (2, 0)])
 @pytest.mark.parametrize("n,N,M", [(64 * 5 + 7, 9, 0), (1 << 12, 64, 4), (64 * 400 + 3, 21, 0), (3000, 50, 50)])
-def test_small_launch_split_kernel_same_bits(nv, torch_cuda, scheme, n, N, M):
+def test_small_launch_split_kernel_same_bits(nv, torch_cuda, scheme, trunc, n, N, M):
     """FP32 launches of fewer than 3 tiles per SM run two warps per tile, one
     path per lane (the one-path form of the step); the tile rows must be the
-    packed kernel's bits, which an explicit launch shape selects."""
+    packed kernel's bits, which an explicit launch shape selects -- for
+    Milstein and Euler under both truncations and for QE (whose two branches
+    the paper's Feller-violating set exercises)."""
     torch = torch_cuda
     cs = [(0, 100.0, 1.0, 0, 0), (1, 95.0, 1.0, 0, M), (0, 105.0, 1.0, 1, 0)]
     n_tiles = -(-n // 64)
@@ -495,7 +497,7 @@ def test_small_launch_split_kernel_same_bits(nv, torch_cuda, scheme, n, N, M):
     for block, grid in ((0, 0), (128, 0), (32, 7)):
         r = torch.full((n_tiles * 12 * len(cs),), float("nan"), dtype=torch.float64, device="cuda")
         opts = nv.make_options(prec=nv.HESTON_FP32, stream=torch.cuda.current_stream(), scheme=scheme,
-                               block_threads=block, grid_ctas=grid)
+                               trunc=trunc, block_threads=block, grid_ctas=grid)
         nv.heston_mc_launch_tiles(_gp(nv, PAPER), _gc(nv, cs), 64 * 1000, n, N, 11, opts, r)
         torch.cuda.synchronize()
         rows.append(r.cpu().numpy())
