@@ -12,6 +12,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _ROOT = os.path.dirname(_HERE)
 SOURCES = [os.path.join(_HERE, "csrc", "heston_mc.cu")]
 HEADERS = [os.path.join(_ROOT, "include", "heston_mc.h"), os.path.join(_HERE, "csrc", "heston_device.cuh"),
+           os.path.join(_HERE, "csrc", "philox.cuh"),
            os.path.join(_HERE, "csrc", "bm64_tables.h")]
 TARGET = os.path.join(_HERE, "libhestonmc.so")
 PEAKS_SOURCES = [os.path.join(_HERE, "csrc", "pipe_peaks.cu")]

@@ -4,7 +4,7 @@
 // multiply (and its low and high 32-bit halves alone) and the three-way xor
 // of Philox4x32-10, the special-function unit (ex2, lg2, sin, cos, rsqrt,
 // sqrt approximations), FP64 FMA, and the FMA-pipe mix of the packed path
-// kernel: 20 wide multiplies per 48 f32x2 FMAs, the heavy-pipe work of one
+// kernel: 15 wide multiplies per 45 f32x2 FMAs, the FMA-pipe work of one
 // lane's two paths over one step.
 //
 // Each thread runs kChains independent dependency chains of one instruction
@@ -30,7 +30,7 @@ enum Kind {
     K_COS = 7, K_RSQRT = 8, K_SQRT = 9, K_DFMA = 10, K_IMAD_LO = 11, K_IMAD_HI = 12, K_MIX = 13,
     K_COUNT = 14
 };
-constexpr int kMixInstsPerUnit = 68;     // 20 wide multiplies + 48 f32x2 FMAs
+constexpr int kMixInstsPerUnit = 60;     // 15 wide multiplies + 45 f32x2 FMAs
 
 __device__ __forceinline__ float mufu(int kind, float x)
 {
@@ -152,21 +152,21 @@ __global__ void peak_kernel(uint32_t iters, float fa, float fb, float *sink)
         for (int i = 0; i < kChains; ++i) s += x[i];
         if (s == 12345u) sink[0] = (float)s;
     } else if constexpr (KIND == K_MIX) {
-        // per unrolled step 5 wide multiplies and 12 f32x2 FMAs on independent
-        // chains: a quarter of one mix unit (20 : 48)
+        // per unrolled step 5 wide multiplies and 15 f32x2 FMAs on independent
+        // chains: a third of one mix unit (15 : 45)
         unsigned long long d[5];
-        float2 x[12];
+        float2 x[15];
         const uint32_t m = 0xD2511F53u ^ (uint32_t)__float_as_uint(fa);
         const float2 a = make_float2(fa, fa), b = make_float2(fb, fb);
 #pragma unroll
         for (int i = 0; i < 5; ++i) d[i] = tid * 2654435761ull + (unsigned long long)i;
 #pragma unroll
-        for (int i = 0; i < 12; ++i) x[i] = make_float2(1.0f + 1e-3f * (float)(tid + i), 1.0f);
+        for (int i = 0; i < 15; ++i) x[i] = make_float2(1.0f + 1e-3f * (float)(tid + i), 1.0f);
         for (uint32_t it = 0; it < iters; ++it) {
 #pragma unroll
             for (int u = 0; u < kUnroll; ++u) {
 #pragma unroll
-                for (int i = 0; i < 12; ++i) {
+                for (int i = 0; i < 15; ++i) {
                     x[i] = __ffma2_rn(x[i], a, b);
                     if (i < 5)
                         asm volatile("mad.wide.u32 %0, %1, %2, %3;" : "=l"(d[i]) : "r"((uint32_t)d[i]), "r"(m), "l"(d[i]));
@@ -178,7 +178,7 @@ __global__ void peak_kernel(uint32_t iters, float fa, float fb, float *sink)
 #pragma unroll
         for (int i = 0; i < 5; ++i) s ^= d[i];
 #pragma unroll
-        for (int i = 0; i < 12; ++i) f += x[i].x + x[i].y;
+        for (int i = 0; i < 15; ++i) f += x[i].x + x[i].y;
         if (s == 12345ull || f == 1234.5f) sink[0] = f + (float)s;
     } else if constexpr (KIND == K_DFMA) {
         double x[kChains];
@@ -243,7 +243,7 @@ const char *pipe_peak_name(int kind)
 // `blocks` x `threads` threads and `iters` loop iterations; d_sink is a device
 // float that the kernel writes only in a case that never happens.  Writes
 // the executed thread-instructions of the measured kind to *thread_insts (for
-// the mix, 68 per unit of 20 wide multiplies and 48 f32x2 FMAs).
+// the mix, 60 per unit of 15 wide multiplies and 45 f32x2 FMAs).
 // Returns 0, or -1 for bad arguments, -2 for a launch error.
 int pipe_peak_launch(int kind, uint32_t blocks, uint32_t threads, uint32_t iters, void *stream,
                      float *d_sink, double *thread_insts)
@@ -270,8 +270,8 @@ int pipe_peak_launch(int kind, uint32_t blocks, uint32_t threads, uint32_t iters
     default: e = launch_kind<K_MIX>(blocks, threads, iters, st, d_sink); break;
     }
     if (e != cudaSuccess) return -2;
-    // the mix: kUnroll quarter-units per iteration, kMixInstsPerUnit instructions per unit
-    *thread_insts = kind == K_MIX ? (double)blocks * threads * (double)iters * kUnroll / 4.0 * kMixInstsPerUnit
+    // the mix: kUnroll third-units per iteration, kMixInstsPerUnit instructions per unit
+    *thread_insts = kind == K_MIX ? (double)blocks * threads * (double)iters * kUnroll / 3.0 * kMixInstsPerUnit
                                   : (double)blocks * threads * (double)iters * kUnroll * kChains;
     return 0;
 }
