@@ -37,24 +37,24 @@ UNIT = "path-steps/s"
 # truncation, European + Asian with a date every step, Vega/Theta tangents,
 # Gamma weights), counted from the operations of the path kernel's
 # formulation:
-#   83.25 scalar operations.  38.25 cannot pack: Philox4x32-10 16 (per path
+#   82.25 scalar operations.  38.25 cannot pack: Philox4x32-10 16 (per path
 #   and block of 2 steps, 15 wide multiplies and 17 xors: the path's round-1
 #   product is loop-invariant and the products of the warp-uniform (step
 #   pair, high path word) come from a per-warp table), the table's 128-bit
 #   load per lane and step pair 0.25, uniform masks + conversions 4,
 #   Box-Muller lg2/sqrt/sin/cos 4 + compare and two factor selects 3,
 #   truncation compare/max/selects 6 (the mean-reversion factor's included)
-#   + rsqrt 1, Milstein-term selects 2, Asian ex2 1, loop 1.  45 are FP32
-#   adds / multiplies / FMAs (uniform scaling 2, Box-Muller 8, step 30, Asian
+#   + rsqrt 1, Milstein-term selects 2, Asian ex2 1, loop 1.  44 are FP32
+#   adds / multiplies / FMAs (uniform scaling 2, Box-Muller 8, step 29, Asian
 #   date 5), which sm_100's f32x2 instructions retire two per issue slot.
-# The issue-slot ceiling is therefore 38.25 + 45/2 = 60.75 thread-instruction
+# The issue-slot ceiling is therefore 38.25 + 44/2 = 60.25 thread-instruction
 # slots per path-step against 1 slot per lane per clock.
-ALGO_OPS_PER_PATH_STEP = 83.25
-ALGO_SLOTS_PER_PATH_STEP = 60.75
+ALGO_OPS_PER_PATH_STEP = 82.25
+ALGO_SLOTS_PER_PATH_STEP = 60.25
 # The persistent batched kernel runs Philox without the table: 20 per
-# path-step (10 wide multiplies and 10 xors), 64.5 slots with an Asian date
+# path-step (10 wide multiplies and 10 xors), 64 slots with an Asian date
 # every step and 3.5 fewer (ex2 + 5 FP32) without one.
-BATCH_SLOTS_PER_PATH_STEP = 64.5
+BATCH_SLOTS_PER_PATH_STEP = 64.0
 # The same work counted one issue slot per operation with Philox at ~45
 # integer operations and no packing: 92 slots per path-step.
 SCALAR_SLOTS_PER_PATH_STEP = 92
@@ -70,16 +70,16 @@ ISSUE_LANES_PER_SM_CLK = 128          # 4 SM sub-partitions x 1 warp-instruction
 FP64_OPS_PER_PATH_STEP = 47
 # The FMA pipe's heavy half, which binds the FP32 path kernel: per warp and
 # lane-step (32 lanes x 2 paths = 64 path-steps) the lane's 15 Philox wide
-# multiplies take about 4 of its cycles each and its 45 f32x2 FMA-pipe
-# instructions 2 each (pipe micro-benchmarks): 150 cycles, one heavy half per
+# multiplies take about 4 of its cycles each and its 44 f32x2 FMA-pipe
+# instructions 2 each (pipe micro-benchmarks): 148 cycles, one heavy half per
 # SM sub-partition.
-HEAVY_CYCLES_PER_LANE_STEP = 150
+HEAVY_CYCLES_PER_LANE_STEP = 148
 HEAVY_LANE_STEP_PATHS = 64
 # The same mix measured: the heavy_mix micro-benchmark runs one lane's FMA-pipe
-# work per step (15 wide multiplies + 45 f32x2 FMAs = 60 instructions, two
-# path-steps) on independent chains; its rate / 60 x 2 is the path-steps/s
+# work per step (15 wide multiplies + 44 f32x2 FMAs = 59 instructions, two
+# path-steps) on independent chains; its rate / 59 x 2 is the path-steps/s
 # ceiling of that mix on this GPU.
-MIX_INSTS_PER_UNIT = 60
+MIX_INSTS_PER_UNIT = 59
 MIX_PATH_STEPS_PER_UNIT = 2
 FLUSH_BYTES = 256 << 20               # > 129 MB L2
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "heston_paths_kernel_multi_strike_2p22.md")
@@ -696,7 +696,7 @@ def run_gpu(args):
         single_ms = e0.elapsed_time(e1) / 2
         same = bool(torch.equal(torch.nan_to_num(bout), torch.nan_to_num(sout)))
         n_unstable = int((~torch.isfinite(bout.view(-1, 12)[:, [3, 5, 9, 11]])).any(dim=1).sum())
-        # roofline of the persistent kernel: algorithmic issue slots per path-step (64.5
+        # roofline of the persistent kernel: algorithmic issue slots per path-step (64
         # with a date every step), less the Asian date (1 + 5/2) where absent
         slots = sum(it.n_paths * it.n_steps * (BATCH_SLOTS_PER_PATH_STEP - 3.5 * (
             1.0 - (min(it.contract.n_monitor or it.n_steps, it.n_steps) / it.n_steps
@@ -704,7 +704,7 @@ def run_gpu(args):
         n_sm_b = torch.cuda.get_device_properties(dev).multi_processor_count
         max_mhz_b = float(_measured_peaks().get("sm_max_mhz") or 2070.0)
         # the measured issue rate (FFMA micro-benchmark), else SMs x 128 lanes x max clock
-        peak_b = (max(v["thread_insts_per_s"] for k_, v in pk.items() if k_ != "heavy_mix") / 1e12 if pk
+        peak_b = (max(v["thread_insts_per_s"] for k_, v in pk.items() if not k_.endswith("_mix")) / 1e12 if pk
                   else n_sm_b * ISSUE_LANES_PER_SM_CLK * max_mhz_b * 1e6 / 1e12)
         ach_b = slots / (batch_ms * 1e-3) / 1e12
         batched = {"workload": f"{len(bitems)} seeded uneven contracts: K~U[70,130], T in {{0.25,0.5,1,2}}, "
@@ -722,8 +722,8 @@ def run_gpu(args):
                    "graph": "memset + persistent kernel + 2 reductions captured, replayed",
                    "roofline": {"bound": "alu", "kernel": "heston_batch_kernel<FULL> (graph replay)",
                                 "achieved": ach_b, "peak": peak_b,
-                                "unit": "T issue slots/s (64.5 per path-step with an Asian date every "
-                                        "step, 61 without; peak: the measured issue rate, as for "
+                                "unit": "T issue slots/s (64 per path-step with an Asian date every "
+                                        "step, 60.5 without; peak: the measured issue rate, as for "
                                         "the path kernel)",
                                 "frac": ach_b / peak_b}}
 
@@ -906,7 +906,7 @@ def run_gpu(args):
         nominal_tinst = n_sm * ISSUE_LANES_PER_SM_CLK * max_mhz * 1e6 / 1e12
         # measured: the FP32 FMA rate, one thread-instruction per lane per clock, the
         # highest rate any instruction kind reaches (the machine's issue rate)
-        peak_tinst = (max(v["thread_insts_per_s"] for k_, v in pk.items() if k_ != "heavy_mix") / 1e12 if pk
+        peak_tinst = (max(v["thread_insts_per_s"] for k_, v in pk.items() if not k_.endswith("_mix")) / 1e12 if pk
                       else nominal_tinst)
         achieved_tinst = path_steps * ALGO_SLOTS_PER_PATH_STEP / (k1 * 1e-3) / 1e12
         pk_clk = clocks.summary_between(*t_pk)
@@ -951,7 +951,7 @@ def run_gpu(args):
                                  PROFILE_SUMMARY, r"sm__pipe_fmaheavy_cycles_active \(of elapsed\) \| \*\*([0-9.]+) %"))
                                  is None else hb / 100.0),
                              "model": "per warp and lane-step (64 path-steps): 15 Philox wide multiplies x 4 "
-                                      "heavy-pipe cycles + 45 f32x2 FMA-pipe instructions x 2 = 150 cycles",
+                                      "heavy-pipe cycles + 44 f32x2 FMA-pipe instructions x 2 = 148 cycles",
                              "ceiling_path_steps_per_s": HEAVY_LANE_STEP_PATHS * 4 * n_sm
                              * (pk_mhz or max_mhz) * 1e6 / HEAVY_CYCLES_PER_LANE_STEP,
                              "frac": (path_steps / (k1 * 1e-3)) / (HEAVY_LANE_STEP_PATHS * 4 * n_sm
@@ -960,7 +960,7 @@ def run_gpu(args):
                              "ceiling_measured_path_steps_per_s": mix_ceiling,
                              "frac_measured": (None if mix_ceiling is None
                                                else (path_steps / (k1 * 1e-3)) / mix_ceiling),
-                             "measured_by": "heavy_mix micro-benchmark (15 wide multiplies + 45 f32x2 "
+                             "measured_by": "heavy_mix micro-benchmark (15 wide multiplies + 44 f32x2 "
                                             "FMAs per lane and step, independent chains, this run)"},
                          "kernel_ms": k1,
                          "path_steps_per_s_kernel": path_steps / (k1 * 1e-3)},

@@ -4,8 +4,10 @@
 // multiply (and its low and high 32-bit halves alone) and the three-way xor
 // of Philox4x32-10, the special-function unit (ex2, lg2, sin, cos, rsqrt,
 // sqrt approximations), FP64 FMA, and the FMA-pipe mix of the packed path
-// kernel: 15 wide multiplies per 45 f32x2 FMAs, the FMA-pipe work of one
-// lane's two paths over one step.
+// kernel: 15 wide multiplies per 44 f32x2 FMAs, the FMA-pipe work of one
+// lane's two paths over one step; and the same FP32 work as scalar FFMAs
+// (15 wide multiplies per 88 FFMAs), which shows whether scalar FFMAs run on
+// the FMA pipe's light half while its heavy half is busy with a multiply.
 //
 // Each thread runs kChains independent dependency chains of one instruction
 // kind in an unrolled loop, so that with enough resident warps the pipe, not
@@ -28,9 +30,10 @@ constexpr int kUnroll = 8;       // chain steps per loop iteration
 enum Kind {
     K_FFMA = 0, K_FFMA2 = 1, K_IMAD_WIDE = 2, K_LOP3 = 3, K_EX2 = 4, K_LG2 = 5, K_SIN = 6,
     K_COS = 7, K_RSQRT = 8, K_SQRT = 9, K_DFMA = 10, K_IMAD_LO = 11, K_IMAD_HI = 12, K_MIX = 13,
-    K_COUNT = 14
+    K_MIX_SCALAR = 14, K_COUNT = 15
 };
-constexpr int kMixInstsPerUnit = 60;     // 15 wide multiplies + 45 f32x2 FMAs
+constexpr int kMixInstsPerUnit = 59;     // 15 wide multiplies + 44 f32x2 FMAs
+constexpr int kMixScalarInstsPerUnit = 103;  // 15 wide multiplies + 88 FFMAs
 
 __device__ __forceinline__ float mufu(int kind, float x)
 {
@@ -152,8 +155,9 @@ __global__ void peak_kernel(uint32_t iters, float fa, float fb, float *sink)
         for (int i = 0; i < kChains; ++i) s += x[i];
         if (s == 12345u) sink[0] = (float)s;
     } else if constexpr (KIND == K_MIX) {
-        // per unrolled step 5 wide multiplies and 15 f32x2 FMAs on independent
-        // chains: a third of one mix unit (15 : 45)
+        // per loop iteration kUnroll mix units of 15 wide multiplies and 44
+        // f32x2 FMAs on independent chains, each unit in three parts of 5 wide
+        // multiplies and 15, 15 and 14 f32x2 FMAs
         unsigned long long d[5];
         float2 x[15];
         const uint32_t m = 0xD2511F53u ^ (uint32_t)__float_as_uint(fa);
@@ -164,10 +168,10 @@ __global__ void peak_kernel(uint32_t iters, float fa, float fb, float *sink)
         for (int i = 0; i < 15; ++i) x[i] = make_float2(1.0f + 1e-3f * (float)(tid + i), 1.0f);
         for (uint32_t it = 0; it < iters; ++it) {
 #pragma unroll
-            for (int u = 0; u < kUnroll; ++u) {
+            for (int u = 0; u < 3 * kUnroll; ++u) {
 #pragma unroll
                 for (int i = 0; i < 15; ++i) {
-                    x[i] = __ffma2_rn(x[i], a, b);
+                    if (i < 14 || u % 3 != 2) x[i] = __ffma2_rn(x[i], a, b);
                     if (i < 5)
                         asm volatile("mad.wide.u32 %0, %1, %2, %3;" : "=l"(d[i]) : "r"((uint32_t)d[i]), "r"(m), "l"(d[i]));
                 }
@@ -179,6 +183,35 @@ __global__ void peak_kernel(uint32_t iters, float fa, float fb, float *sink)
         for (int i = 0; i < 5; ++i) s ^= d[i];
 #pragma unroll
         for (int i = 0; i < 15; ++i) f += x[i].x + x[i].y;
+        if (s == 12345ull || f == 1234.5f) sink[0] = f + (float)s;
+    } else if constexpr (KIND == K_MIX_SCALAR) {
+        // per loop iteration kUnroll units of 15 wide multiplies and 88 FFMAs
+        // on independent chains, each unit in three parts of 5 wide multiplies
+        // and 30, 30 and 28 FFMAs
+        unsigned long long d[5];
+        float x[30];
+        const uint32_t m = 0xD2511F53u ^ (uint32_t)__float_as_uint(fa);
+#pragma unroll
+        for (int i = 0; i < 5; ++i) d[i] = tid * 2654435761ull + (unsigned long long)i;
+#pragma unroll
+        for (int i = 0; i < 30; ++i) x[i] = 1.0f + 1e-3f * (float)(tid + i);
+        for (uint32_t it = 0; it < iters; ++it) {
+#pragma unroll
+            for (int u = 0; u < 3 * kUnroll; ++u) {
+#pragma unroll
+                for (int i = 0; i < 30; ++i) {
+                    if (i < 28 || u % 3 != 2) x[i] = __fmaf_rn(x[i], fa, fb);
+                    if (i < 5)
+                        asm volatile("mad.wide.u32 %0, %1, %2, %3;" : "=l"(d[i]) : "r"((uint32_t)d[i]), "r"(m), "l"(d[i]));
+                }
+            }
+        }
+        unsigned long long s = 0;
+        float f = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 5; ++i) s ^= d[i];
+#pragma unroll
+        for (int i = 0; i < 30; ++i) f += x[i];
         if (s == 12345ull || f == 1234.5f) sink[0] = f + (float)s;
     } else if constexpr (KIND == K_DFMA) {
         double x[kChains];
@@ -235,7 +268,7 @@ const char *pipe_peak_name(int kind)
 {
     static const char *names[K_COUNT] = {"ffma", "ffma2", "imad_wide", "lop3", "mufu_ex2", "mufu_lg2",
                                          "mufu_sin", "mufu_cos", "mufu_rsqrt", "mufu_sqrt", "dfma",
-                                         "imad_lo", "imad_hi", "heavy_mix"};
+                                         "imad_lo", "imad_hi", "heavy_mix", "scalar_mix"};
     return (kind >= 0 && kind < K_COUNT) ? names[kind] : "";
 }
 
@@ -243,7 +276,8 @@ const char *pipe_peak_name(int kind)
 // `blocks` x `threads` threads and `iters` loop iterations; d_sink is a device
 // float that the kernel writes only in a case that never happens.  Writes
 // the executed thread-instructions of the measured kind to *thread_insts (for
-// the mix, 60 per unit of 15 wide multiplies and 45 f32x2 FMAs).
+// the mixes, 59 per unit of 15 wide multiplies and 44 f32x2 FMAs and 103 per
+// unit of 15 wide multiplies and 88 FFMAs).
 // Returns 0, or -1 for bad arguments, -2 for a launch error.
 int pipe_peak_launch(int kind, uint32_t blocks, uint32_t threads, uint32_t iters, void *stream,
                      float *d_sink, double *thread_insts)
@@ -267,12 +301,15 @@ int pipe_peak_launch(int kind, uint32_t blocks, uint32_t threads, uint32_t iters
     case K_DFMA: e = launch_kind<K_DFMA>(blocks, threads, iters, st, d_sink); break;
     case K_IMAD_LO: e = launch_kind<K_IMAD_LO>(blocks, threads, iters, st, d_sink); break;
     case K_IMAD_HI: e = launch_kind<K_IMAD_HI>(blocks, threads, iters, st, d_sink); break;
-    default: e = launch_kind<K_MIX>(blocks, threads, iters, st, d_sink); break;
+    case K_MIX: e = launch_kind<K_MIX>(blocks, threads, iters, st, d_sink); break;
+    default: e = launch_kind<K_MIX_SCALAR>(blocks, threads, iters, st, d_sink); break;
     }
     if (e != cudaSuccess) return -2;
-    // the mix: kUnroll third-units per iteration, kMixInstsPerUnit instructions per unit
-    *thread_insts = kind == K_MIX ? (double)blocks * threads * (double)iters * kUnroll / 3.0 * kMixInstsPerUnit
-                                  : (double)blocks * threads * (double)iters * kUnroll * kChains;
+    // the mix: kUnroll units per iteration, kMixInstsPerUnit instructions per unit
+    const double per_iter = kind == K_MIX ? (double)kUnroll * kMixInstsPerUnit
+                          : kind == K_MIX_SCALAR ? (double)kUnroll * kMixScalarInstsPerUnit
+                          : (double)kUnroll * kChains;
+    *thread_insts = (double)blocks * threads * (double)iters * per_iter;
     return 0;
 }
 

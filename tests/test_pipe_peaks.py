@@ -5,8 +5,10 @@ CPU: the library loads, names its kinds, and rejects bad arguments before
 any CUDA call.  GPU: every kind runs; the FP32 FMA rate is one
 thread-instruction per lane per clock (the issue rate) and the highest of the
 single kinds; the f32x2 FMA rate is half of it; the FMA-pipe mix of the path
-kernel (15 wide multiplies per 45 f32x2 FMAs) is no faster than either of its
-parts alone allows."""
+kernel (15 wide multiplies per 44 f32x2 FMAs) is no faster than either of its
+parts alone allows; and the same FP32 work as scalar FFMAs costs the sum of
+its parts (scalar FFMAs do not run beside the wide multiplies), which is why
+the path kernel packs its FP32 work into f32x2 instructions."""
 import ctypes
 import os
 
@@ -15,7 +17,7 @@ import pytest
 from paper_2309_10477_gb300 import peaks
 
 KINDS = ["ffma", "ffma2", "imad_wide", "lop3", "mufu_ex2", "mufu_lg2", "mufu_sin", "mufu_cos",
-         "mufu_rsqrt", "mufu_sqrt", "dfma", "imad_lo", "imad_hi", "heavy_mix"]
+         "mufu_rsqrt", "mufu_sqrt", "dfma", "imad_lo", "imad_hi", "heavy_mix", "scalar_mix"]
 
 
 @pytest.fixture(scope="module")
@@ -50,10 +52,15 @@ def test_rates_are_consistent(lib):
     # one FP32 FMA per lane per clock, 128 lanes per SM, at 1.0-2.2 GHz
     per_sm_clk_max = rate["ffma"] / (n_sm * 1.0e9)
     assert 0.85 * 128 * 1.0 <= per_sm_clk_max <= 1.02 * 128 * 2.2
-    single = {k: v for k, v in rate.items() if k != "heavy_mix"}
+    single = {k: v for k, v in rate.items() if not k.endswith("_mix")}
     assert max(single, key=single.get) == "ffma"
     assert 0.45 <= rate["ffma2"] / rate["ffma"] <= 0.55
-    # the mix: a unit of 15 wide multiplies and 45 f32x2 FMAs takes at least as
+    # the mix: a unit of 15 wide multiplies and 44 f32x2 FMAs takes at least as
     # long as either part alone at its own rate
-    unit = rate["heavy_mix"] / 60.0
-    assert unit <= 1.02 / max(15.0 / rate["imad_wide"], 45.0 / rate["ffma2"])
+    unit = rate["heavy_mix"] / 59.0
+    assert unit <= 1.02 / max(15.0 / rate["imad_wide"], 44.0 / rate["ffma2"])
+    # the scalar mix: 15 wide multiplies and 88 FFMAs take at least 0.9 of the
+    # sum of their times alone, and no less time than the packed mix
+    t_scalar = 103.0 / rate["scalar_mix"]
+    assert t_scalar >= 0.9 * (15.0 / rate["imad_wide"] + 88.0 / rate["ffma"])
+    assert t_scalar >= 0.95 * (59.0 / rate["heavy_mix"])
