@@ -811,9 +811,11 @@ def run_gpu(args):
         submit_s = time.perf_counter() - t0
         st_mid = srv.stats()
         submitted.set()
+        th_w.join()
+        # the largest of the 10 ms samples and the count at the last arrival
+        queued_max[0] = max(queued_max[0], int(st_mid.queued + st_mid.active))
         th_c.join()
         wall_s = time.perf_counter() - t0
-        th_w.join()
         clocks.mark(False)
         st1 = srv.stats()
         # capacity: 2000 requests of the same stream submitted at once, against the
