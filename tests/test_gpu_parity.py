@@ -423,9 +423,14 @@ def test_cached_scratch_reuse_and_release(nv):
         nv.heston_release_cached_memory(64)
 
 
-@pytest.mark.parametrize("prec,path_begin,n", [("fp32", 0, 64 * 3 + 19), ("fp64", 0, 64 * 3 + 19),
-                                                ("fp32", (1 << 32) - 128, 256 - 5)])
-def test_tile_rows_are_the_sums_of_the_per_path_records(nv, torch_cuda, prec, path_begin, n):
+@pytest.mark.parametrize("prec,path_begin,n,N,block,scheme", [("fp32", 0, 64 * 3 + 19, 30, 0, 0),
+                                                               ("fp64", 0, 64 * 3 + 19, 30, 0, 0),
+                                                               ("fp32", (1 << 32) - 128, 256 - 5, 30, 0, 0),
+                                                               ("fp32", (1 << 32) - 128, 256 - 5, 67, 128, 0),
+                                                               ("fp32", 64 * 7, 64 * 5 + 3, 130, 128, 0),
+                                                               ("fp32", (1 << 32) - 128, 256 - 5, 67, 128, 2)])
+def test_tile_rows_are_the_sums_of_the_per_path_records(nv, torch_cuda, prec, path_begin, n, N, block,
+                                                        scheme):
     """The production path kernel and the per-path record kernel (the one the
     per-path parity tests check against the oracle) compute the same paths:
     each tile row equals, bit for bit, the warp's sums of the per-path
@@ -433,21 +438,27 @@ def test_tile_rows_are_the_sums_of_the_per_path_records(nv, torch_cuda, prec, pa
     fma(x0, x0, x1 * x1), zero past the last path), then a xor butterfly over
     offsets 16, 8, 4, 2, 1 -- rounded in the path precision.  The third case
     runs a path range across index 2^32, where the Philox counter's high
-    word (taken per tile in the path kernel) changes."""
+    word (taken per tile in the path kernel) changes.  These small launches
+    take the split kernel (one path per lane); block = 128 selects the packed
+    kernel, whose Philox words come from the per-warp table of 32 step pairs:
+    across 2^32 (one CTA whose warps have different high words) with 33
+    step pairs and an odd last step, and over 65 step pairs (three fills of
+    the table); the last case runs QE (scheme 2) the same way."""
     from fractions import Fraction
     torch = torch_cuda
     bits = 24 if prec == "fp32" else 53
-    cs = _contracts_for(30)
+    cs = _contracts_for(N)
     nc = len(cs)
-    N, seed = 30, 5
-    opts = nv.make_options(prec=_prec(nv, prec), stream=torch.cuda.current_stream())
+    seed = 5
+    opts = nv.make_options(prec=_prec(nv, prec), stream=torch.cuda.current_stream(), block_threads=block,
+                           scheme=scheme)
     n_tiles = -(-n // 64)
     rows = torch.zeros(n_tiles * 12 * nc, dtype=torch.float64, device="cuda")
     nv.heston_mc_launch_tiles(_gp(nv, BASE), _gc(nv, cs), path_begin, n, N, seed, opts, rows)
     torch.cuda.synchronize()
     rows = rows.cpu().numpy().reshape(n_tiles, 12 * nc)
     _, est = nv.heston_mc_debug_paths(_gp(nv, BASE), _gc(nv, cs), N, seed,
-                                      nv.make_options(prec=_prec(nv, prec)),
+                                      nv.make_options(prec=_prec(nv, prec), scheme=scheme),
                                       path_begin + np.arange(n, dtype=np.uint64))
     rnd = lambda q: round_exact(q, bits)
     for t in range(n_tiles):
