@@ -35,8 +35,16 @@ UNIT = "path-steps/s"
 
 # Algorithmic work per path-step for this workload (FP32 path, full
 # truncation, European + Asian with a date every step, Vega/Theta tangents,
-# Gamma weights), counted from the operations of the path kernel's
-# formulation:
+# Gamma weights).  The roofline's per-unit figure is the method's count, one
+# issue slot per operation: Philox4x32-10 half a block ~45 INT32 operations
+# (10 rounds x 2 wide multiplies + ~6 xors/adds, per 2 steps), Box-Muller 4
+# MUFU + ~6 FP32, correlation and W 3, log-price 1 MUFU + ~4, variance ~7,
+# Asian date 1 MUFU + 3, Vega/Theta tangents ~16, Gamma weight 2: about 45
+# INT32 + 41 FP32 + 6 MUFU = 92 slots per path-step (88 without an Asian
+# date).
+METHOD_SLOTS_PER_PATH_STEP = 92
+METHOD_SLOTS_NO_DATE = 88
+# The path kernel's own formulation needs fewer:
 #   82.25 scalar operations.  38.25 cannot pack: Philox4x32-10 16 (per path
 #   and block of 2 steps, 15 wide multiplies and 17 xors: the path's round-1
 #   product is loop-invariant and the products of the warp-uniform (step
@@ -47,7 +55,7 @@ UNIT = "path-steps/s"
 #   + rsqrt 1, Milstein-term selects 2, Asian ex2 1, loop 1.  44 are FP32
 #   adds / multiplies / FMAs (uniform scaling 2, Box-Muller 8, step 29, Asian
 #   date 5), which sm_100's f32x2 instructions retire two per issue slot.
-# The issue-slot ceiling is therefore 38.25 + 44/2 = 60.25 thread-instruction
+# Its issue-slot minimum is therefore 38.25 + 44/2 = 60.25 thread-instruction
 # slots per path-step against 1 slot per lane per clock.
 ALGO_OPS_PER_PATH_STEP = 82.25
 ALGO_SLOTS_PER_PATH_STEP = 60.25
@@ -55,9 +63,6 @@ ALGO_SLOTS_PER_PATH_STEP = 60.25
 # path-step (10 wide multiplies and 10 xors), 64 slots with an Asian date
 # every step and 3.5 fewer (ex2 + 5 FP32) without one.
 BATCH_SLOTS_PER_PATH_STEP = 64.0
-# The same work counted one issue slot per operation with Philox at ~45
-# integer operations and no packing: 92 slots per path-step.
-SCALAR_SLOTS_PER_PATH_STEP = 92
 ISSUE_LANES_PER_SM_CLK = 128          # 4 SM sub-partitions x 1 warp-instruction x 32 lanes
 # FP64 path (one European call): the explicit FP64 arithmetic per path-step,
 # counted from the operations the method needs -- the Milstein step with its
@@ -696,17 +701,24 @@ def run_gpu(args):
         single_ms = e0.elapsed_time(e1) / 2
         same = bool(torch.equal(torch.nan_to_num(bout), torch.nan_to_num(sout)))
         n_unstable = int((~torch.isfinite(bout.view(-1, 12)[:, [3, 5, 9, 11]])).any(dim=1).sum())
-        # roofline of the persistent kernel: algorithmic issue slots per path-step (64
-        # with a date every step), less the Asian date (1 + 5/2) where absent
-        slots = sum(it.n_paths * it.n_steps * (BATCH_SLOTS_PER_PATH_STEP - 3.5 * (
-            1.0 - (min(it.contract.n_monitor or it.n_steps, it.n_steps) / it.n_steps
-                   if it.contract.payoff == nv.HESTON_ASIAN_ARITH else 0.0))) for it in bitems)
+        # roofline of the persistent kernel: the method's issue slots per path-step (92
+        # with an Asian date every step, 88 without), and the kernel's own minimum (64
+        # with a date every step, 3.5 fewer without: ex2 + 5 FP32 packed two per slot)
+        def date_frac(it):
+            return (min(it.contract.n_monitor or it.n_steps, it.n_steps) / it.n_steps
+                    if it.contract.payoff == nv.HESTON_ASIAN_ARITH else 0.0)
+        slots = sum(it.n_paths * it.n_steps * (METHOD_SLOTS_NO_DATE + (METHOD_SLOTS_PER_PATH_STEP
+                                                                      - METHOD_SLOTS_NO_DATE) * date_frac(it))
+                    for it in bitems)
+        slots_kernel = sum(it.n_paths * it.n_steps * (BATCH_SLOTS_PER_PATH_STEP - 3.5 * (1.0 - date_frac(it)))
+                           for it in bitems)
         n_sm_b = torch.cuda.get_device_properties(dev).multi_processor_count
         max_mhz_b = float(_measured_peaks().get("sm_max_mhz") or 2070.0)
         # the measured issue rate (FFMA micro-benchmark), else SMs x 128 lanes x max clock
         peak_b = (max(v["thread_insts_per_s"] for k_, v in pk.items() if not k_.endswith("_mix")) / 1e12 if pk
                   else n_sm_b * ISSUE_LANES_PER_SM_CLK * max_mhz_b * 1e6 / 1e12)
         ach_b = slots / (batch_ms * 1e-3) / 1e12
+        ach_bk = slots_kernel / (batch_ms * 1e-3) / 1e12
         batched = {"workload": f"{len(bitems)} seeded uneven contracts: K~U[70,130], T in {{0.25,0.5,1,2}}, "
                                "paths 2^U (U~U[14,20]), steps 50..500, European/Asian 50/50, FP32",
                    "total_path_steps": int(plan.total_path_steps),
@@ -722,10 +734,13 @@ def run_gpu(args):
                    "graph": "memset + persistent kernel + 2 reductions captured, replayed",
                    "roofline": {"bound": "alu", "kernel": "heston_batch_kernel<FULL> (graph replay)",
                                 "achieved": ach_b, "peak": peak_b,
-                                "unit": "T issue slots/s (64 per path-step with an Asian date every "
-                                        "step, 60.5 without; peak: the measured issue rate, as for "
+                                "unit": "T issue slots/s (92 per path-step with an Asian date every "
+                                        "step, 88 without; peak: the measured issue rate, as for "
                                         "the path kernel)",
-                                "frac": ach_b / peak_b}}
+                                "frac": ach_b / peak_b,
+                                "kernel_slot_model": {"slots_per_path_step": "64 with an Asian date "
+                                                      "every step, 60.5 without",
+                                                      "achieved": ach_bk, "frac": ach_bk / peak_b}}}
 
     # adjoint gradient: 252-step Asian call, 2^20 paths, d price / d (S0, v0, kappa, theta, xi, rho, r)
     adjoint = None
@@ -910,7 +925,8 @@ def run_gpu(args):
         # highest rate any instruction kind reaches (the machine's issue rate)
         peak_tinst = (max(v["thread_insts_per_s"] for k_, v in pk.items() if not k_.endswith("_mix")) / 1e12 if pk
                       else nominal_tinst)
-        achieved_tinst = path_steps * ALGO_SLOTS_PER_PATH_STEP / (k1 * 1e-3) / 1e12
+        achieved_tinst = path_steps * METHOD_SLOTS_PER_PATH_STEP / (k1 * 1e-3) / 1e12
+        achieved_kernel = path_steps * ALGO_SLOTS_PER_PATH_STEP / (k1 * 1e-3) / 1e12
         pk_clk = clocks.summary_between(*t_pk)
         pk_mhz = pk_clk.get("sm_mhz") or max_mhz
         traffic = _profiled_traffic()
@@ -935,17 +951,22 @@ def run_gpu(args):
             "gpu_launches": 3 * args.steps * world,         # path kernel + 2 reductions per step, all ranks
             "roofline": {"bound": "alu", "kernel": "heston_paths_kernel<float,FULL,ASIAN>",
                          "achieved": achieved_tinst, "peak": peak_tinst,
-                         "unit": f"T issue slots/s ({ALGO_SLOTS_PER_PATH_STEP} algorithmic slots per "
-                                 f"path-step: {ALGO_OPS_PER_PATH_STEP} operations, FP32 ones packed "
-                                 "two per f32x2 instruction; peak = the measured issue rate, the "
-                                 "FP32 FMA micro-benchmark's thread-instructions/s)",
+                         "unit": f"T issue slots/s ({METHOD_SLOTS_PER_PATH_STEP} algorithmic issue slots per "
+                                 "path-step, one per operation the method computes: ~45 INT32 (Philox) "
+                                 "+ ~41 FP32 + 6 MUFU; peak = the measured issue rate, the FP32 FMA "
+                                 "micro-benchmark's thread-instructions/s)",
                          "peak_source": ("measured (pipe_peaks, this run)" if pk else
                                          "nominal: SMs x 128 lanes x max clock (--no-peaks)"),
                          "nominal_peak": nominal_tinst,
-                         "ops_per_s": path_steps * ALGO_OPS_PER_PATH_STEP / (k1 * 1e-3) / 1e12,
                          "frac": achieved_tinst / peak_tinst,
-                         "frac_92_slot_model": path_steps * SCALAR_SLOTS_PER_PATH_STEP / (k1 * 1e-3)
-                         / 1e12 / peak_tinst,
+                         "kernel_slot_model": {
+                             "slots_per_path_step": ALGO_SLOTS_PER_PATH_STEP,
+                             "ops_per_path_step": ALGO_OPS_PER_PATH_STEP,
+                             "note": "the path kernel's own minimum: FP32 operations packed two per "
+                                     "f32x2 instruction, Philox's warp-uniform products from a per-warp "
+                                     "table and its per-path round-1 product hoisted out of the loop",
+                             "achieved": achieved_kernel, "frac": achieved_kernel / peak_tinst,
+                             "ops_per_s": path_steps * ALGO_OPS_PER_PATH_STEP / (k1 * 1e-3) / 1e12},
                          "traffic": traffic,
                          "binding_pipe": {
                              "pipe": "fmaheavy (the FMA pipe's heavy half)",
