@@ -428,7 +428,9 @@ def test_cached_scratch_reuse_and_release(nv):
                                                                ("fp32", (1 << 32) - 128, 256 - 5, 30, 0, 0),
                                                                ("fp32", (1 << 32) - 128, 256 - 5, 67, 128, 0),
                                                                ("fp32", 64 * 7, 64 * 5 + 3, 130, 128, 0),
-                                                               ("fp32", (1 << 32) - 128, 256 - 5, 67, 128, 2)])
+                                                               ("fp32", (1 << 32) - 128, 256 - 5, 67, 128, 2),
+                                                               ("fp32", 0, 64 * 2 + 5, 1, 128, 0),
+                                                               ("fp32", 0, 64 * 2 + 5, 2, 128, 0)])
 def test_tile_rows_are_the_sums_of_the_per_path_records(nv, torch_cuda, prec, path_begin, n, N, block,
                                                         scheme):
     """The production path kernel and the per-path record kernel (the one the
@@ -443,7 +445,8 @@ def test_tile_rows_are_the_sums_of_the_per_path_records(nv, torch_cuda, prec, pa
     kernel, whose Philox words come from the per-warp table of 32 step pairs:
     across 2^32 (one CTA whose warps have different high words) with 33
     step pairs and an odd last step, and over 65 step pairs (three fills of
-    the table); the last case runs QE (scheme 2) the same way."""
+    the table); QE (scheme 2) the same way; and one step (no step pair: the
+    odd step alone) and two (one step pair)."""
     from fractions import Fraction
     torch = torch_cuda
     bits = 24 if prec == "fp32" else 53
