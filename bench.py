@@ -46,7 +46,7 @@ METHOD_SLOTS_PER_PATH_STEP = 92
 METHOD_SLOTS_NO_DATE = 88
 # The path kernel's own formulation needs fewer:
 #   82.25 scalar operations.  38.25 cannot pack: Philox4x32-10 16 (per path
-#   and block of 2 steps, 15 wide multiplies and 17 xors: the path's round-1
+#   and block of 2 steps, 15 wide multiplies and 17 xors: the path's R1
 #   product is loop-invariant and the products of the warp-uniform (step
 #   pair, high path word) come from a per-warp table), the table's 128-bit
 #   load per lane and step pair 0.25, uniform masks + conversions 4,
@@ -964,7 +964,7 @@ def run_gpu(args):
                              "ops_per_path_step": ALGO_OPS_PER_PATH_STEP,
                              "note": "the path kernel's own minimum: FP32 operations packed two per "
                                      "f32x2 instruction, Philox's warp-uniform products from a per-warp "
-                                     "table and its per-path round-1 product hoisted out of the loop",
+                                     "table and its per-path second-round product hoisted out of the loop",
                              "achieved": achieved_kernel, "frac": achieved_kernel / peak_tinst,
                              "ops_per_s": path_steps * ALGO_OPS_PER_PATH_STEP / (k1 * 1e-3) / 1e12},
                          "traffic": traffic,

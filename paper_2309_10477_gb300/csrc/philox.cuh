@@ -42,14 +42,14 @@ __host__ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, PhiloxKey key)
     return c;
 }
 
-// The split of philox4x32_10((j, p, h, 0), key).  With A = j M0 and B = h M1,
-// round 0 gives (hi(B) ^ p ^ k0, lo(B), hi(A) ^ k1, lo(A)); round 1 multiplies
-// x1 = p ^ hi(B) ^ k0 (P1 = x1 M0, per path, free of j) and z1 = hi(A) ^ k1
-// (Q = z1 M1, per (j, h)); round 2 multiplies x2 = hi(Q) ^ lo(B) ^ k0' (P2,
-// per (j, h)) and z2 = hi(P1) ^ lo(A) ^ k1' (per path).  philox_head returns
-// the (j, h) words with their round keys folded in:
-// (lo(A) ^ k1', lo(Q) ^ k0'', hi(P2) ^ k1'', lo(P2)), where ' and '' are the
-// keys of rounds 1 and 2; lo_b = lo(B).
+// The split of philox4x32_10((j, p, h, 0), key), with the rounds numbered R0
+// to R9.  With A = j M0 and B = h M1, R0 gives (hi(B) ^ p ^ k0, lo(B),
+// hi(A) ^ k1, lo(A)); R1 multiplies x1 = p ^ hi(B) ^ k0 (P1 = x1 M0, per path,
+// free of j) and z1 = hi(A) ^ k1 (Q = z1 M1, per (j, h)); R2 multiplies
+// x2 = hi(Q) ^ lo(B) ^ k0' (P2, per (j, h)) and z2 = hi(P1) ^ lo(A) ^ k1'
+// (per path).  philox_head returns the (j, h) words with their round keys
+// folded in: (lo(A) ^ k1', lo(Q) ^ k0'', hi(P2) ^ k1'', lo(P2)), where ' and ''
+// mark the keys of R1 and R2; lo_b = lo(B).
 __host__ __device__ __forceinline__ uint4 philox_head(uint32_t j, uint32_t lo_b, PhiloxKey key)
 {
     const unsigned long long A = (unsigned long long)j * kPhiloxM0;
@@ -67,7 +67,7 @@ __host__ __device__ __forceinline__ unsigned long long philox_p1(uint32_t p, uin
     return (unsigned long long)(p ^ hi_b ^ key.k0) * kPhiloxM0;
 }
 
-// Rounds 1 (its per-path half) to 9 from the head t and the path's P1.
+// R1 (its per-path half) to R9 from the head t and the path's P1.
 __host__ __device__ __forceinline__ uint4 philox_tail(uint4 t, unsigned long long P1, PhiloxKey key)
 {
     const uint32_t z2 = (uint32_t)(P1 >> 32) ^ t.x;

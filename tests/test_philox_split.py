@@ -1,5 +1,5 @@
 """The path kernel's split Philox4x32-10 (csrc/philox.cuh: the warp-uniform
-(step pair, high path word) part of rounds 0-2 computed once per warp, the
+(step pair, high path word) part of its first three rounds computed once per warp, the
 rest per path) gives the same words as the plain ten rounds, and both equal
 the oracle's Philox4x32-10 (itself pinned to cuRAND's host generator).
 Compiled here as a host program; no GPU."""
